@@ -1,0 +1,193 @@
+/*
+ * pb_spgemm.h -- C ABI of the GB300 PB-SpGEMM library (libpbspgemm.so).
+ *
+ * Computes C = A * B for sparse A (m x k, CSC) and B (k x n, CSR) with the
+ * propagation-blocking outer-product method of Gu, Moreira, Edelsohn and Azad
+ * (arXiv 2002.11302, Alg. 2):
+ *   symbolic  Alg. 3 flop count per column/row k, plus the per-row flop count
+ *             (Sec. III-B) that cuts rows into bins;
+ *   expand    the outer products A(:,k) * B(k,:) become (key, value) tuples
+ *             written into row-range bins (propagation blocking, Sec. III-A/C);
+ *   sort      each bin is sorted on-chip by its packed (in-bin row, column) key
+ *             (Sec. III-D);
+ *   compress  equal keys are summed (Sec. III-E) and the merged bins are
+ *             written in row order as CSR (ConvertCSR, Alg. 2).
+ *
+ * Conventions for every entry point:
+ *   - All matrix and workspace pointers are DEVICE pointers owned by the
+ *     caller.  The library never frees caller memory.  Host pointers are only
+ *     the struct arguments themselves and the output scalars of query calls.
+ *   - Index arrays are int32.  Input pointer arrays (colptr, rowptr) are int32
+ *     and monotone with ptr[0] = 0.  Entry order inside a column of A or a row
+ *     of B is arbitrary.  No duplicate (row, col) inside one operand.
+ *   - Output C: column indices strictly ascending inside each row; every
+ *     structural product is kept, including exact-zero sums (Sec. III-E
+ *     merges without dropping).
+ *   - Every call returns pb_status; nothing throws across the ABI.  A call
+ *     that returns an error leaves its outputs unspecified.
+ *     pb_last_error() gives a message for the last failing call on a handle.
+ *   - Compute calls are asynchronous on the given stream unless stated.
+ *     Errors detected on the device (capacity, overflow, bounded-wait
+ *     timeout) are recorded in a device status word read by pb_plan_status
+ *     after the stream has been synchronised.
+ */
+#ifndef PB_SPGEMM_H
+#define PB_SPGEMM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *pb_stream_t; /* same object as cudaStream_t; NULL = legacy default stream */
+
+typedef enum pb_status {
+    PB_OK = 0,
+    PB_ERR_INVALID_ARG = 1,       /* null pointer, negative size, bad config value */
+    PB_ERR_SHAPE = 2,             /* A.ncols != B.nrows, or C shape differs from m x n */
+    PB_ERR_UNSUPPORTED_DTYPE = 3,
+    PB_ERR_OOM = 4,               /* the allocator returned NULL */
+    PB_ERR_OVERFLOW = 5,          /* nnz(C) exceeds C's capacity or an int32 row pointer */
+    PB_ERR_CUDA = 6,              /* a CUDA runtime call failed (message in pb_last_error) */
+    PB_ERR_TIMEOUT = 7,           /* a bounded device-side wait expired */
+    PB_ERR_BUSY = 8,              /* a request can never be admitted under the server budget */
+    PB_ERR_UNSUPPORTED = 9,       /* a size outside what this build handles (message says which) */
+    PB_ERR_WORKSPACE = 10         /* workspace smaller than pb_plan_query reported */
+} pb_status;
+
+/* Value types.  Tuples are the intermediate (key, value) pairs of Alg. 2. */
+typedef enum pb_dtype {
+    PB_F64 = 0,          /* A, B, C values double; double tuples (12-byte tuples)              */
+    PB_F32 = 1,          /* A, B, C values float; float products and tuples, merged in double  */
+    PB_F64_F32TUPLE = 2  /* A, B, C values double; products rounded once to float in the tuple
+                            (8-byte tuples), merged in double                                  */
+} pb_dtype;
+
+typedef struct pb_csc {   /* A: nrows x ncols, column j holds rowidx/val[colptr[j] .. colptr[j+1]) */
+    int32_t nrows, ncols;
+    int64_t nnz;
+    const int32_t *colptr; /* device, ncols + 1 */
+    const int32_t *rowidx; /* device, nnz */
+    const void *val;       /* device, nnz values of the dtype's input type */
+} pb_csc;
+
+typedef struct pb_csr {   /* B: nrows x ncols, row i holds colidx/val[rowptr[i] .. rowptr[i+1]) */
+    int32_t nrows, ncols;
+    int64_t nnz;
+    const int32_t *rowptr; /* device, nrows + 1 */
+    const int32_t *colidx; /* device, nnz */
+    const void *val;       /* device, nnz */
+} pb_csr;
+
+typedef struct pb_csr_out { /* C: nrows x ncols in CSR; exactly one of rowptr64/rowptr32 non-null */
+    int32_t nrows, ncols;
+    int64_t cap;           /* entries available in colidx / val; c_cap from pb_plan_query always suffices */
+    int64_t *rowptr64;     /* device, nrows + 1 (int64 row pointer)                                  */
+    int32_t *rowptr32;     /* device, nrows + 1 (int32 row pointer; PB_ERR_OVERFLOW if nnz >= 2^31)   */
+    int32_t *colidx;       /* device, cap */
+    void *val;             /* device, cap values of the dtype's output type */
+    int64_t *nnz_dev;      /* device, 1 element receiving nnz(C); may be NULL */
+} pb_csr_out;
+
+/* Tunables.  Zero in any field selects the built-in default. */
+typedef struct pb_config {
+    int32_t bin_capacity;    /* max tuples of one bin sorted on-chip (power of two, 1024..16384) */
+    int32_t sort_threads;    /* threads of one sort CTA (256 or 512)                           */
+    int32_t expand_chunk;    /* tuples per expand work item                                     */
+    int32_t reserved0;
+    int64_t max_tuple_bytes; /* cap on the tuple workspace; larger products run in row panels    */
+    int64_t reserved1;
+} pb_config;
+
+typedef struct pb_handle pb_handle;
+typedef struct pb_plan pb_plan;
+
+/* Device-memory provider used for plan-owned arrays.  alloc returns a device
+ * pointer (256-byte aligned) or NULL; free releases it.  Both are stream
+ * ordered on the stream passed.  Default: cudaMallocAsync / cudaFreeAsync. */
+typedef void *(*pb_alloc_fn)(size_t bytes, pb_stream_t stream, void *ctx);
+typedef void (*pb_free_fn)(void *ptr, size_t bytes, pb_stream_t stream, void *ctx);
+
+/* Create a handle bound to the current CUDA device.  *h receives the handle. */
+pb_status pb_create(pb_handle **h);
+pb_status pb_destroy(pb_handle *h);
+/* Replace the device-memory provider (NULL alloc restores the default). */
+pb_status pb_set_allocator(pb_handle *h, pb_alloc_fn alloc, pb_free_fn free_fn, void *ctx);
+/* Message for the last failing call on this handle ("" if none).  Owned by the handle. */
+const char *pb_last_error(const pb_handle *h);
+/* Library version as major*10000 + minor*100 + patch. */
+int32_t pb_version(void);
+
+/*
+ * Symbolic phase (Alg. 3 and Sec. III-B): computes flop, the per-row flop
+ * histogram and the row-range bins.  Launches on `stream`, then synchronises
+ * it ONCE to read the sizes back.  The plan owns device arrays allocated
+ * through the handle's allocator; it stays valid for numeric calls on any
+ * A, B with the same sparsity structure (values may change).
+ * cfg may be NULL.  Errors: INVALID_ARG, SHAPE, UNSUPPORTED_DTYPE, OOM, CUDA,
+ * UNSUPPORTED (a key of row offset and column does not fit 32 bits).
+ */
+pb_status pb_spgemm_symbolic(pb_handle *h, const pb_csc *A, const pb_csr *B, pb_dtype dtype,
+                             const pb_config *cfg, pb_stream_t stream, pb_plan **plan);
+
+/* Sizes of a plan.  Any output pointer may be NULL.
+ *   flop             total multiplications (Alg. 3)
+ *   c_cap            entries C must hold (= flop, since nnz(C) <= flop)
+ *   workspace_bytes  device workspace pb_spgemm_numeric needs
+ *   nbins            number of bins (all panels)
+ *   npanels          number of row panels (1 unless max_tuple_bytes forces more) */
+pb_status pb_plan_query(const pb_plan *plan, int64_t *flop, int64_t *c_cap, size_t *workspace_bytes,
+                        int64_t *nbins, int32_t *npanels);
+
+/*
+ * Numeric phase (Alg. 2 expand, sort, compress, ConvertCSR).  Asynchronous on
+ * `stream`: no host synchronisation, no allocation.  `workspace` is a device
+ * buffer of at least workspace_bytes, 256-byte aligned; it is scratch and may
+ * be reused after the stream reaches this call's end.  A and B must have the
+ * structure the plan was made from.  C->cap must be >= nnz(C) (c_cap always
+ * suffices); otherwise the device records PB_ERR_OVERFLOW and writes nothing
+ * past cap.  Errors: INVALID_ARG, SHAPE, WORKSPACE, CUDA.
+ */
+pb_status pb_spgemm_numeric(pb_handle *h, const pb_plan *plan, const pb_csc *A, const pb_csr *B,
+                            pb_csr_out *C, void *workspace, size_t ws_bytes, pb_stream_t stream);
+
+/* Device-side status of the last numeric call made with this plan: PB_OK or
+ * the first device-detected error.  Synchronises `stream` first. */
+pb_status pb_plan_status(const pb_plan *plan, pb_stream_t stream, pb_status *device_status);
+
+/* Copy plan arrays to caller DEVICE buffers (any may be NULL), for tests and tools.
+ *   F       int64 [A.ncols + 1]  exclusive prefix of per-k flop (Alg. 3)
+ *   R       int64 [A.nrows + 1]  exclusive prefix of per-row flop (Sec. III-B)
+ *   bin_row int32 [nbins + 1]    first row of each bin, bin_row[nbins] = A.nrows
+ *   bin_off int64 [nbins + 1]    tuple offset of each bin in the workspace (padded)
+ * Synchronises `stream`. */
+pb_status pb_plan_export(const pb_plan *plan, int64_t *F, int64_t *R, int32_t *bin_row, int64_t *bin_off,
+                         pb_stream_t stream);
+
+/* Run only the expand phase into `workspace` (same layout numeric uses):
+ * tuples of bin b occupy [bin_off[b], bin_off[b] + count_b) of the key array
+ * that starts at workspace and the value array that starts at
+ * workspace + pb_debug_values_offset(plan).  For tests of the expand step. */
+pb_status pb_debug_expand(pb_handle *h, const pb_plan *plan, const pb_csc *A, const pb_csr *B,
+                          void *workspace, size_t ws_bytes, pb_stream_t stream);
+size_t pb_debug_values_offset(const pb_plan *plan);
+
+pb_status pb_plan_destroy(pb_plan *plan);
+
+/* Measurement hooks (no counterpart in the paper; they only observe).
+ * pb_set_phase_events: when events is non-NULL, every later numeric call on
+ * this handle records events[0] before its first launch, events[1] after the
+ * workspace reset, events[2] after the expand kernel and events[3] after the
+ * sort/compress kernel, on the call's stream.  The four entries are cudaEvent_t
+ * handles owned by the caller; NULL disables recording.
+ * pb_kernel_launches: number of CUDA kernels this library has launched in the
+ * process so far (all handles). */
+pb_status pb_set_phase_events(pb_handle *h, void *const *events);
+int64_t pb_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PB_SPGEMM_H */

@@ -62,11 +62,15 @@ def _load():
             lib.pb_oracle_row_flop.argtypes = [i32, i32, i32p, i32p, i32p, i64p]
             lib.pb_oracle_expand.restype = None
             lib.pb_oracle_expand.argtypes = [i32, i32p, i32p, f64p, i32p, i32p, f64p, i32p, i32p, f64p]
+            lib.pb_oracle_prepare.restype = ctypes.c_void_p
+            lib.pb_oracle_prepare.argtypes = [i32, i32, i32p, i32p, f64p]
+            lib.pb_oracle_release.restype = None
+            lib.pb_oracle_release.argtypes = [ctypes.c_void_p]
             lib.pb_oracle_spgemm_count.restype = ctypes.c_int
-            lib.pb_oracle_spgemm_count.argtypes = [i32, i32, i32, i32p, i32p, i32p, i32p, i64, i64p, i64p]
+            lib.pb_oracle_spgemm_count.argtypes = [ctypes.c_void_p, i32, i32p, i32p, i64, i64p, i64p]
             lib.pb_oracle_spgemm_fill.restype = ctypes.c_int
-            lib.pb_oracle_spgemm_fill.argtypes = [i32, i32, i32, i32p, i32p, f64p, i32p, i32p, f64p,
-                                                  i64, i64p, i64p, i32p, f64p, f64p]
+            lib.pb_oracle_spgemm_fill.argtypes = [ctypes.c_void_p, i32, i32p, i32p, f64p, i64, i64p, i64p,
+                                                  i32p, f64p, f64p]
             _lib = lib
     return _lib
 
@@ -147,25 +151,28 @@ def spgemm(A, B, rows=None) -> Product:
     rows = np.ascontiguousarray(rows, dtype=np.int64)
     colptrA, rowidxA, valA = _i32(A.colptr), _i32(A.rowidx), _f64(A.val)
     rowptrB, colidxB, valB = _i32(B.rowptr), _i32(B.colidx), _f64(B.val)
-    cnt = np.zeros(rows.shape[0], dtype=np.int64)
-    rc = lib.pb_oracle_spgemm_count(A.nrows, A.ncols, B.ncols, _p(colptrA, ctypes.c_int32),
-                                    _p(rowidxA, ctypes.c_int32), _p(rowptrB, ctypes.c_int32),
-                                    _p(colidxB, ctypes.c_int32), rows.shape[0], _p(rows, ctypes.c_int64),
-                                    _p(cnt, ctypes.c_int64))
-    if rc != 0:
-        raise MemoryError("oracle count pass failed")
-    ptr = np.zeros(rows.shape[0] + 1, dtype=np.int64)
-    np.cumsum(cnt, out=ptr[1:])
-    nnz = int(ptr[-1])
-    col = np.empty(max(nnz, 1), np.int32)
-    val = np.empty(max(nnz, 1), np.float64)
-    absval = np.empty(max(nnz, 1), np.float64)
-    rc = lib.pb_oracle_spgemm_fill(A.nrows, A.ncols, B.ncols, _p(colptrA, ctypes.c_int32),
-                                   _p(rowidxA, ctypes.c_int32), _p(valA, ctypes.c_double),
-                                   _p(rowptrB, ctypes.c_int32), _p(colidxB, ctypes.c_int32),
-                                   _p(valB, ctypes.c_double), rows.shape[0], _p(rows, ctypes.c_int64),
-                                   _p(ptr, ctypes.c_int64), _p(col, ctypes.c_int32),
-                                   _p(val, ctypes.c_double), _p(absval, ctypes.c_double))
-    if rc != 0:
-        raise MemoryError("oracle fill pass failed")
+    ctx = lib.pb_oracle_prepare(A.nrows, A.ncols, _p(colptrA, ctypes.c_int32), _p(rowidxA, ctypes.c_int32),
+                                _p(valA, ctypes.c_double))
+    if not ctx:
+        raise MemoryError("oracle: row view of A")
+    try:
+        cnt = np.zeros(rows.shape[0], dtype=np.int64)
+        rc = lib.pb_oracle_spgemm_count(ctx, B.ncols, _p(rowptrB, ctypes.c_int32), _p(colidxB, ctypes.c_int32),
+                                        rows.shape[0], _p(rows, ctypes.c_int64), _p(cnt, ctypes.c_int64))
+        if rc != 0:
+            raise MemoryError("oracle count pass failed")
+        ptr = np.zeros(rows.shape[0] + 1, dtype=np.int64)
+        np.cumsum(cnt, out=ptr[1:])
+        nnz = int(ptr[-1])
+        col = np.empty(max(nnz, 1), np.int32)
+        val = np.empty(max(nnz, 1), np.float64)
+        absval = np.empty(max(nnz, 1), np.float64)
+        rc = lib.pb_oracle_spgemm_fill(ctx, B.ncols, _p(rowptrB, ctypes.c_int32), _p(colidxB, ctypes.c_int32),
+                                       _p(valB, ctypes.c_double), rows.shape[0], _p(rows, ctypes.c_int64),
+                                       _p(ptr, ctypes.c_int64), _p(col, ctypes.c_int32),
+                                       _p(val, ctypes.c_double), _p(absval, ctypes.c_double))
+        if rc != 0:
+            raise MemoryError("oracle fill pass failed")
+    finally:
+        lib.pb_oracle_release(ctx)
     return Product(rows, ptr, col[:nnz], val[:nnz], absval[:nnz])

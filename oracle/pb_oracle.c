@@ -81,40 +81,69 @@ void pb_oracle_expand(int32_t k, const int32_t *colptrA, const int32_t *rowidxA,
 }
 
 /* Row view of A: A is given by columns; Gustavson walks it by rows.  A stable
- * counting sort by row id keeps the entries of each row in ascending k. */
+ * counting sort by row id keeps the entries of each row in ascending k.  Each
+ * thread owns a block of rows and scans all of A, placing only its own rows,
+ * so the scatter runs in parallel without shared writes. */
 typedef struct {
+    int32_t m;
     int64_t *ptr;   /* m+1 */
     int32_t *col;   /* nnz: the k of each entry */
     double *val;
 } rows_of_A;
 
-static int build_rows_of_A(int32_t m, int32_t k, const int32_t *colptrA, const int32_t *rowidxA,
-                           const double *valA, rows_of_A *R) {
+void pb_oracle_release(void *ctx) {
+    rows_of_A *R = (rows_of_A *)ctx;
+    if (!R) return;
+    free(R->ptr); free(R->col); free(R->val); free(R);
+}
+
+void *pb_oracle_prepare(int32_t m, int32_t k, const int32_t *colptrA, const int32_t *rowidxA,
+                        const double *valA) {
     int64_t nnz = colptrA[k];
+    rows_of_A *R = (rows_of_A *)calloc(1, sizeof(rows_of_A));
+    if (!R) return NULL;
+    R->m = m;
     R->ptr = (int64_t *)calloc((size_t)m + 1, sizeof(int64_t));
     R->col = (int32_t *)malloc((size_t)(nnz > 0 ? nnz : 1) * sizeof(int32_t));
     R->val = (double *)malloc((size_t)(nnz > 0 ? nnz : 1) * sizeof(double));
-    int64_t *fill = (int64_t *)malloc(((size_t)m + 1) * sizeof(int64_t));
-    if (!R->ptr || !R->col || !R->val || !fill) {
-        free(R->ptr); free(R->col); free(R->val); free(fill);
-        return -1;
+    if (!R->ptr || !R->col || !R->val) {
+        pb_oracle_release(R);
+        return NULL;
     }
     for (int64_t e = 0; e < nnz; ++e) R->ptr[rowidxA[e] + 1] += 1;
     for (int32_t r = 0; r < m; ++r) R->ptr[r + 1] += R->ptr[r];
-    memcpy(fill, R->ptr, ((size_t)m + 1) * sizeof(int64_t));
-    for (int32_t i = 0; i < k; ++i) {
-        for (int32_t e = colptrA[i]; e < colptrA[i + 1]; ++e) {
-            int64_t p = fill[rowidxA[e]]++;
-            R->col[p] = i;
-            R->val[p] = valA ? valA[e] : 0.0;
+    int failed = 0;
+#pragma omp parallel
+    {
+        int nt = 1, t = 0;
+#ifdef _OPENMP
+        nt = omp_get_num_threads();
+        t = omp_get_thread_num();
+#endif
+        int32_t r0 = (int32_t)((int64_t)m * t / nt), r1 = (int32_t)((int64_t)m * (t + 1) / nt);
+        int64_t *fill = (int64_t *)malloc(((size_t)(r1 - r0) + 1) * sizeof(int64_t));
+        if (!fill) {
+#pragma omp atomic write
+            failed = 1;
+        } else {
+            for (int32_t r = r0; r < r1; ++r) fill[r - r0] = R->ptr[r];
+            for (int32_t i = 0; i < k; ++i) {
+                for (int32_t e = colptrA[i]; e < colptrA[i + 1]; ++e) {
+                    int32_t r = rowidxA[e];
+                    if (r < r0 || r >= r1) continue;
+                    int64_t p = fill[r - r0]++;
+                    R->col[p] = i;
+                    R->val[p] = valA ? valA[e] : 0.0;
+                }
+            }
+            free(fill);
         }
     }
-    free(fill);
-    return 0;
-}
-
-static void free_rows_of_A(rows_of_A *R) {
-    free(R->ptr); free(R->col); free(R->val);
+    if (failed) {
+        pb_oracle_release(R);
+        return NULL;
+    }
+    return R;
 }
 
 static int cmp_i32(const void *a, const void *b) {
@@ -123,12 +152,9 @@ static int cmp_i32(const void *a, const void *b) {
 }
 
 /* Structural count of C(i,:) for each listed row.  Returns 0, or -1 on OOM. */
-int pb_oracle_spgemm_count(int32_t m, int32_t k, int32_t n,
-                           const int32_t *colptrA, const int32_t *rowidxA,
-                           const int32_t *rowptrB, const int32_t *colidxB,
+int pb_oracle_spgemm_count(const void *ctx, int32_t n, const int32_t *rowptrB, const int32_t *colidxB,
                            int64_t nrows_list, const int64_t *rows, int64_t *row_nnz) {
-    rows_of_A R;
-    if (build_rows_of_A(m, k, colptrA, rowidxA, NULL, &R) != 0) return -1;
+    const rows_of_A *R = (const rows_of_A *)ctx;
     int failed = 0;
 #pragma omp parallel
     {
@@ -145,8 +171,8 @@ int pb_oracle_spgemm_count(int32_t m, int32_t k, int32_t n,
             if (!stamp) continue;
             int64_t i = rows[t];
             int64_t cnt = 0;
-            for (int64_t p = R.ptr[i]; p < R.ptr[i + 1]; ++p) {
-                int32_t kk = R.col[p];
+            for (int64_t p = R->ptr[i]; p < R->ptr[i + 1]; ++p) {
+                int32_t kk = R->col[p];
                 for (int32_t eb = rowptrB[kk]; eb < rowptrB[kk + 1]; ++eb) {
                     int32_t j = colidxB[eb];
                     if (stamp[j] != t) { stamp[j] = t; ++cnt; }
@@ -156,19 +182,15 @@ int pb_oracle_spgemm_count(int32_t m, int32_t k, int32_t n,
         }
         free(stamp);
     }
-    free_rows_of_A(&R);
     return failed ? -1 : 0;
 }
 
 /* Values of C(i,:) for each listed row: out_ptr[t] is where row t starts in the
  * output arrays (from pb_oracle_spgemm_count).  Columns ascending. */
-int pb_oracle_spgemm_fill(int32_t m, int32_t k, int32_t n,
-                          const int32_t *colptrA, const int32_t *rowidxA, const double *valA,
-                          const int32_t *rowptrB, const int32_t *colidxB, const double *valB,
-                          int64_t nrows_list, const int64_t *rows, const int64_t *out_ptr,
+int pb_oracle_spgemm_fill(const void *ctx, int32_t n, const int32_t *rowptrB, const int32_t *colidxB,
+                          const double *valB, int64_t nrows_list, const int64_t *rows, const int64_t *out_ptr,
                           int32_t *out_col, double *out_val, double *out_abs) {
-    rows_of_A R;
-    if (build_rows_of_A(m, k, colptrA, rowidxA, valA, &R) != 0) return -1;
+    const rows_of_A *R = (const rows_of_A *)ctx;
     int failed = 0;
 #pragma omp parallel
     {
@@ -188,9 +210,9 @@ int pb_oracle_spgemm_fill(int32_t m, int32_t k, int32_t n,
             int64_t i = rows[t];
             int32_t *list = out_col + out_ptr[t];
             int64_t cnt = 0;
-            for (int64_t p = R.ptr[i]; p < R.ptr[i + 1]; ++p) {
-                int32_t kk = R.col[p];
-                double a = R.val[p];
+            for (int64_t p = R->ptr[i]; p < R->ptr[i + 1]; ++p) {
+                int32_t kk = R->col[p];
+                double a = R->val[p];
                 for (int32_t eb = rowptrB[kk]; eb < rowptrB[kk + 1]; ++eb) {
                     int32_t j = colidxB[eb];
                     double prod = a * valB[eb];
@@ -212,6 +234,5 @@ int pb_oracle_spgemm_fill(int32_t m, int32_t k, int32_t n,
         }
         free(acc); free(acc_abs); free(stamp);
     }
-    free_rows_of_A(&R);
     return failed ? -1 : 0;
 }

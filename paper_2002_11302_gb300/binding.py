@@ -1,0 +1,333 @@
+"""Thin Python binding of libpbspgemm (ctypes over the C ABI in include/pb_spgemm.h).
+
+Only argument marshalling lives here: torch tensors become device pointers,
+the current torch stream becomes the cudaStream_t, and torch's caching
+allocator provides the plan's device memory.  Every step of the product runs
+in the CUDA library; there is no CPU path.  If the library cannot be built or
+loaded the calls raise.
+
+Names follow the C ABI: ``symbolic`` / ``numeric`` / ``plan_status`` mirror
+``pb_spgemm_symbolic`` / ``pb_spgemm_numeric`` / ``pb_plan_status``.
+"""
+from __future__ import annotations
+
+import ctypes
+import threading
+from dataclasses import dataclass
+from typing import Optional
+
+import numpy as np
+import torch
+
+from . import build as _build
+
+PB_F64, PB_F32, PB_F64_F32TUPLE = 0, 1, 2
+STATUS_NAMES = {0: "PB_OK", 1: "PB_ERR_INVALID_ARG", 2: "PB_ERR_SHAPE", 3: "PB_ERR_UNSUPPORTED_DTYPE",
+                4: "PB_ERR_OOM", 5: "PB_ERR_OVERFLOW", 6: "PB_ERR_CUDA", 7: "PB_ERR_TIMEOUT", 8: "PB_ERR_BUSY",
+                9: "PB_ERR_UNSUPPORTED", 10: "PB_ERR_WORKSPACE"}
+_IN_DTYPE = {PB_F64: torch.float64, PB_F32: torch.float32, PB_F64_F32TUPLE: torch.float64}
+_OUT_DTYPE = _IN_DTYPE
+
+
+class PBError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        self.status = status
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+
+
+class _CSC(ctypes.Structure):
+    _fields_ = [("nrows", ctypes.c_int32), ("ncols", ctypes.c_int32), ("nnz", ctypes.c_int64),
+                ("colptr", ctypes.c_void_p), ("rowidx", ctypes.c_void_p), ("val", ctypes.c_void_p)]
+
+
+class _CSR(ctypes.Structure):
+    _fields_ = [("nrows", ctypes.c_int32), ("ncols", ctypes.c_int32), ("nnz", ctypes.c_int64),
+                ("rowptr", ctypes.c_void_p), ("colidx", ctypes.c_void_p), ("val", ctypes.c_void_p)]
+
+
+class _CSROut(ctypes.Structure):
+    _fields_ = [("nrows", ctypes.c_int32), ("ncols", ctypes.c_int32), ("cap", ctypes.c_int64),
+                ("rowptr64", ctypes.c_void_p), ("rowptr32", ctypes.c_void_p), ("colidx", ctypes.c_void_p),
+                ("val", ctypes.c_void_p), ("nnz_dev", ctypes.c_void_p)]
+
+
+class _Config(ctypes.Structure):
+    _fields_ = [("bin_capacity", ctypes.c_int32), ("sort_threads", ctypes.c_int32),
+                ("expand_chunk", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+                ("max_tuple_bytes", ctypes.c_int64), ("reserved1", ctypes.c_int64)]
+
+
+_ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+_FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+
+# Exported symbols of the library with their C signatures (kept in step with the header).
+_VP, _I32, _I64, _SZ = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t
+SIGNATURES = {
+    "pb_version": (_I32, []),
+    "pb_create": (ctypes.c_int, [ctypes.POINTER(_VP)]),
+    "pb_destroy": (ctypes.c_int, [_VP]),
+    "pb_set_allocator": (ctypes.c_int, [_VP, _ALLOC_FN, _FREE_FN, _VP]),
+    "pb_last_error": (ctypes.c_char_p, [_VP]),
+    "pb_spgemm_symbolic": (ctypes.c_int, [_VP, ctypes.POINTER(_CSC), ctypes.POINTER(_CSR), ctypes.c_int,
+                                          ctypes.POINTER(_Config), _VP, ctypes.POINTER(_VP)]),
+    "pb_plan_query": (ctypes.c_int, [_VP, ctypes.POINTER(_I64), ctypes.POINTER(_I64), ctypes.POINTER(_SZ),
+                                     ctypes.POINTER(_I64), ctypes.POINTER(_I32)]),
+    "pb_spgemm_numeric": (ctypes.c_int, [_VP, _VP, ctypes.POINTER(_CSC), ctypes.POINTER(_CSR),
+                                         ctypes.POINTER(_CSROut), _VP, _SZ, _VP]),
+    "pb_plan_status": (ctypes.c_int, [_VP, _VP, ctypes.POINTER(ctypes.c_int)]),
+    "pb_plan_export": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP]),
+    "pb_debug_expand": (ctypes.c_int, [_VP, _VP, ctypes.POINTER(_CSC), ctypes.POINTER(_CSR), _VP, _SZ, _VP]),
+    "pb_debug_values_offset": (_SZ, [_VP]),
+    "pb_plan_destroy": (ctypes.c_int, [_VP]),
+    "pb_set_phase_events": (ctypes.c_int, [_VP, _VP]),
+    "pb_kernel_launches": (_I64, []),
+}
+
+_lib = None
+_lib_lock = threading.Lock()
+
+
+def load_library(path: Optional[str] = None):
+    """Build (if stale) and load libpbspgemm.so; declare every exported symbol."""
+    global _lib
+    with _lib_lock:
+        if _lib is None:
+            lib = ctypes.CDLL(path or _build.build())
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(lib, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = lib
+    return _lib
+
+
+# ---------------------------------------------------------------------------
+# Device-memory provider: torch's caching allocator.
+# ---------------------------------------------------------------------------
+@_ALLOC_FN
+def _torch_alloc(nbytes, stream, ctx):
+    try:
+        return torch.cuda.caching_allocator_alloc(int(nbytes), stream=int(stream or 0))
+    except Exception:  # noqa: BLE001 - an allocation failure becomes PB_ERR_OOM in the library
+        return None
+
+
+@_FREE_FN
+def _torch_free(ptr, nbytes, stream, ctx):
+    if ptr:
+        torch.cuda.caching_allocator_delete(int(ptr))
+
+
+# ---------------------------------------------------------------------------
+# Matrices on the device.
+# ---------------------------------------------------------------------------
+@dataclass
+class CscMatrix:
+    nrows: int
+    ncols: int
+    colptr: torch.Tensor  # int32 [ncols+1]
+    rowidx: torch.Tensor  # int32 [nnz]
+    val: torch.Tensor
+
+    @property
+    def nnz(self) -> int:
+        return int(self.rowidx.numel())
+
+    def _c(self) -> _CSC:
+        return _CSC(self.nrows, self.ncols, self.nnz, self.colptr.data_ptr(), self.rowidx.data_ptr() or None,
+                    self.val.data_ptr() or None)
+
+
+@dataclass
+class CsrMatrix:
+    nrows: int
+    ncols: int
+    rowptr: torch.Tensor  # int32 or int64 [nrows+1]
+    colidx: torch.Tensor  # int32 [nnz]
+    val: torch.Tensor
+
+    @property
+    def nnz(self) -> int:
+        return int(self.colidx.numel())
+
+    def _c(self) -> _CSR:
+        if self.rowptr.dtype != torch.int32:
+            raise PBError(1, "input CSR row pointers must be int32")
+        return _CSR(self.nrows, self.ncols, self.nnz, self.rowptr.data_ptr(), self.colidx.data_ptr() or None,
+                    self.val.data_ptr() or None)
+
+
+def _dev(a: np.ndarray, device, dtype=None) -> torch.Tensor:
+    t = torch.from_numpy(np.ascontiguousarray(a))
+    if dtype is not None:
+        t = t.to(dtype)
+    return t.to(device)
+
+
+def csc_to_device(A, device="cuda", val_dtype=None) -> CscMatrix:
+    """Copy a host CSC (any object with nrows/ncols/colptr/rowidx/val) to the device."""
+    return CscMatrix(A.nrows, A.ncols, _dev(A.colptr, device, torch.int32), _dev(A.rowidx, device, torch.int32),
+                     _dev(A.val, device, val_dtype))
+
+
+def csr_to_device(B, device="cuda", val_dtype=None) -> CsrMatrix:
+    return CsrMatrix(B.nrows, B.ncols, _dev(B.rowptr, device, torch.int32), _dev(B.colidx, device, torch.int32),
+                     _dev(B.val, device, val_dtype))
+
+
+def _stream_ptr(stream) -> Optional[int]:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream) or None
+
+
+def _check(lib, h, status: int):
+    if status != 0:
+        msg = lib.pb_last_error(h).decode() if h else ""
+        raise PBError(status, msg)
+
+
+class Handle:
+    """pb_handle bound to the current device; plan memory comes from torch."""
+
+    def __init__(self, use_torch_allocator: bool = True):
+        self.lib = load_library()
+        h = ctypes.c_void_p()
+        _check(self.lib, None, self.lib.pb_create(ctypes.byref(h)))
+        self.ptr = h
+        if use_torch_allocator:
+            _check(self.lib, h, self.lib.pb_set_allocator(h, _torch_alloc, _torch_free, None))
+
+    def __del__(self):
+        if getattr(self, "ptr", None):
+            self.lib.pb_destroy(self.ptr)
+            self.ptr = None
+
+
+def set_phase_events(handle: "Handle", events) -> None:
+    """Record four torch.cuda.Event objects around the numeric phases (None disables)."""
+    if events is None:
+        _check(handle.lib, handle.ptr, handle.lib.pb_set_phase_events(handle.ptr, None))
+        return
+    arr = (ctypes.c_void_p * 4)(*[int(e.cuda_event) for e in events])
+    handle._events = (events, arr)  # keep alive
+    _check(handle.lib, handle.ptr, handle.lib.pb_set_phase_events(handle.ptr, arr))
+
+
+def kernel_launches() -> int:
+    return int(load_library().pb_kernel_launches())
+
+
+_default_handle = None
+
+
+def default_handle() -> Handle:
+    global _default_handle
+    if _default_handle is None:
+        _default_handle = Handle()
+    return _default_handle
+
+
+def make_config(bin_capacity: int = 0, expand_chunk: int = 0, max_tuple_bytes: int = 0) -> _Config:
+    return _Config(bin_capacity, 0, expand_chunk, 0, max_tuple_bytes, 0)
+
+
+class Plan:
+    """Result of the symbolic phase; owns plan arrays on the device."""
+
+    def __init__(self, handle: Handle, ptr: ctypes.c_void_p, dtype: int, A: CscMatrix, B: CsrMatrix):
+        self.handle, self.ptr, self.dtype = handle, ptr, dtype
+        self.m, self.k, self.n = A.nrows, A.ncols, B.ncols
+        flop, ccap, nbins = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        ws, npan = ctypes.c_size_t(), ctypes.c_int32()
+        _check(handle.lib, handle.ptr, handle.lib.pb_plan_query(ptr, ctypes.byref(flop), ctypes.byref(ccap),
+                                                                 ctypes.byref(ws), ctypes.byref(nbins),
+                                                                 ctypes.byref(npan)))
+        self.flop, self.c_cap, self.workspace_bytes = flop.value, ccap.value, ws.value
+        self.nbins, self.npanels = nbins.value, npan.value
+
+    def __del__(self):
+        if getattr(self, "ptr", None):
+            self.handle.lib.pb_plan_destroy(self.ptr)
+            self.ptr = None
+
+    def status(self, stream=None) -> int:
+        st = ctypes.c_int()
+        _check(self.handle.lib, self.handle.ptr,
+               self.handle.lib.pb_plan_status(self.ptr, _stream_ptr(stream), ctypes.byref(st)))
+        return st.value
+
+    def export(self, stream=None):
+        """(F, R, bin_row, bin_off) device tensors copied out of the plan."""
+        dev = torch.device("cuda")
+        F = torch.empty(self.k + 1, dtype=torch.int64, device=dev)
+        R = torch.empty(self.m + 1, dtype=torch.int64, device=dev)
+        br = torch.empty(self.nbins + 1, dtype=torch.int32, device=dev)
+        bo = torch.empty(self.nbins + 1, dtype=torch.int64, device=dev)
+        _check(self.handle.lib, self.handle.ptr,
+               self.handle.lib.pb_plan_export(self.ptr, F.data_ptr(), R.data_ptr(), br.data_ptr(), bo.data_ptr(),
+                                              _stream_ptr(stream)))
+        return F, R, br, bo
+
+    def workspace(self) -> torch.Tensor:
+        return torch.empty(max(self.workspace_bytes, 256), dtype=torch.uint8, device="cuda")
+
+
+def symbolic(A: CscMatrix, B: CsrMatrix, dtype: int = PB_F64, config: Optional[_Config] = None,
+             handle: Optional[Handle] = None, stream=None) -> Plan:
+    h = handle or default_handle()
+    for t, want in ((A.val, _IN_DTYPE.get(dtype)), (B.val, _IN_DTYPE.get(dtype))):
+        if want is not None and t.dtype != want:
+            raise PBError(3, f"values must be {want} for dtype {dtype}")
+    cA, cB = A._c(), B._c()
+    out = ctypes.c_void_p()
+    cfg = ctypes.byref(config) if config is not None else None
+    _check(h.lib, h.ptr, h.lib.pb_spgemm_symbolic(h.ptr, ctypes.byref(cA), ctypes.byref(cB), dtype, cfg,
+                                                  _stream_ptr(stream), ctypes.byref(out)))
+    return Plan(h, out, dtype, A, B)
+
+
+def numeric(plan: Plan, A: CscMatrix, B: CsrMatrix, C: CsrMatrix, workspace: torch.Tensor,
+            nnz_out: Optional[torch.Tensor] = None, stream=None) -> None:
+    """Run expand + sort + compress into C (C.colidx / C.val sized to its capacity)."""
+    h = plan.handle
+    cA, cB = A._c(), B._c()
+    r64 = C.rowptr.data_ptr() if C.rowptr.dtype == torch.int64 else None
+    r32 = C.rowptr.data_ptr() if C.rowptr.dtype == torch.int32 else None
+    cC = _CSROut(C.nrows, C.ncols, C.colidx.numel(), r64, r32, C.colidx.data_ptr() or None,
+                 C.val.data_ptr() or None, nnz_out.data_ptr() if nnz_out is not None else None)
+    _check(h.lib, h.ptr, h.lib.pb_spgemm_numeric(h.ptr, plan.ptr, ctypes.byref(cA), ctypes.byref(cB),
+                                                 ctypes.byref(cC), workspace.data_ptr(), workspace.numel(),
+                                                 _stream_ptr(stream)))
+
+
+def debug_expand(plan: Plan, A: CscMatrix, B: CsrMatrix, workspace: torch.Tensor, stream=None):
+    """Run only the expand phase; returns (keys uint32-as-int32 view, values) views of the workspace."""
+    h = plan.handle
+    cA, cB = A._c(), B._c()
+    _check(h.lib, h.ptr, h.lib.pb_debug_expand(h.ptr, plan.ptr, ctypes.byref(cA), ctypes.byref(cB),
+                                               workspace.data_ptr(), workspace.numel(), _stream_ptr(stream)))
+    return workspace, int(h.lib.pb_debug_values_offset(plan.ptr))
+
+
+def alloc_output(plan: Plan, rowptr64: bool = True, cap: Optional[int] = None) -> CsrMatrix:
+    cap = plan.c_cap if cap is None else cap
+    dev = torch.device("cuda")
+    return CsrMatrix(plan.m, plan.n,
+                     torch.empty(plan.m + 1, dtype=torch.int64 if rowptr64 else torch.int32, device=dev),
+                     torch.empty(max(cap, 1), dtype=torch.int32, device=dev),
+                     torch.empty(max(cap, 1), dtype=_OUT_DTYPE[plan.dtype], device=dev))
+
+
+def spgemm(A: CscMatrix, B: CsrMatrix, dtype: int = PB_F64, config: Optional[_Config] = None,
+           rowptr64: bool = True, handle: Optional[Handle] = None) -> CsrMatrix:
+    """C = A * B on the current stream; returns C trimmed to nnz(C).  Synchronises."""
+    plan = symbolic(A, B, dtype, config, handle)
+    C = alloc_output(plan, rowptr64)
+    ws = plan.workspace()
+    numeric(plan, A, B, C, ws)
+    st = plan.status()
+    if st != 0:
+        raise PBError(st, "device-side error in the numeric phase")
+    nnz = int(C.rowptr[-1].item())
+    return CsrMatrix(C.nrows, C.ncols, C.rowptr, C.colidx[:nnz], C.val[:nnz])

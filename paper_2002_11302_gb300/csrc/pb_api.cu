@@ -1,0 +1,470 @@
+// Host side of the C ABI: handles, plans, argument checks, workspace layout
+// and the launch sequence of the symbolic and numeric phases.
+#include <atomic>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "pb_common.cuh"
+
+using namespace pb;
+
+struct pb_handle {
+    int device = 0;
+    int num_sms = 0;
+    pb_alloc_fn alloc = nullptr;
+    pb_free_fn free_fn = nullptr;
+    void *ctx = nullptr;
+    std::string last_error;
+    cudaEvent_t phase_ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    bool phase_on = false;
+};
+
+namespace pb {
+static std::atomic<int64_t> g_launches{0};
+void count_launches(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+}  // namespace pb
+
+struct pb_plan {
+    pb_handle *h = nullptr;
+    int32_t m = 0, k = 0, n = 0;
+    int64_t nnzA = 0, nnzB = 0;
+    pb_dtype dtype = PB_F64;
+    int32_t colbits = 1, rmax_log2 = 0, capacity = 4096;
+    int64_t heavy = 0, chunk = 1024, nchunks = 0;
+    PlanHeader hdr{};
+    // device arrays (one arena + the chunk table)
+    void *arena = nullptr;
+    size_t arena_bytes = 0;
+    void *chunk_mem = nullptr;
+    size_t chunk_bytes = 0;
+    int64_t *F = nullptr, *R = nullptr, *flags = nullptr, *bin_off = nullptr, *scan_tmp = nullptr;
+    uint64_t *rowinfo = nullptr;
+    int32_t *bin_row = nullptr, *chunk_k = nullptr;
+    PlanHeader *dhdr = nullptr;
+    uint32_t *err = nullptr;
+    // workspace layout of the numeric phase
+    size_t ws_keys = 0, ws_vals = 0, ws_cursor = 0, ws_status = 0, ws_ctrl = 0, ws_bytes = 0;
+};
+
+namespace {
+
+constexpr int32_t kVersion = 1 * 10000 + 0 * 100 + 0;
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+void *default_alloc(size_t bytes, pb_stream_t stream, void *) {
+    void *p = nullptr;
+    if (cudaMallocAsync(&p, bytes ? bytes : 256, reinterpret_cast<cudaStream_t>(stream)) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return nullptr;
+    }
+    return p;
+}
+
+void default_free(void *p, size_t, pb_stream_t stream, void *) {
+    if (p) (void)cudaFreeAsync(p, reinterpret_cast<cudaStream_t>(stream));
+}
+
+pb_status fail(pb_handle *h, pb_status st, const std::string &msg) {
+    if (h) h->last_error = msg;
+    return st;
+}
+
+pb_status cuda_fail(pb_handle *h, cudaError_t e, const char *where) {
+    std::string msg = std::string(where) + ": " + cudaGetErrorString(e);
+    return fail(h, PB_ERR_CUDA, msg);
+}
+
+#define PB_CUDA(h, call)                                         \
+    do {                                                         \
+        cudaError_t e_ = (call);                                 \
+        if (e_ != cudaSuccess) return cuda_fail((h), e_, #call); \
+    } while (0)
+
+int ceil_log2_u64(uint64_t x) {
+    int b = 0;
+    while ((uint64_t(1) << b) < x) ++b;
+    return b;
+}
+
+size_t tuple_val_bytes(pb_dtype d) { return d == PB_F64 ? 8 : 4; }
+
+bool valid_dtype(pb_dtype d) { return d == PB_F64 || d == PB_F32 || d == PB_F64_F32TUPLE; }
+
+pb_status check_operands(pb_handle *h, const pb_csc *A, const pb_csr *B) {
+    if (!A || !B) return fail(h, PB_ERR_INVALID_ARG, "A and B must not be NULL");
+    if (A->nrows < 0 || A->ncols < 0 || B->nrows < 0 || B->ncols < 0 || A->nnz < 0 || B->nnz < 0)
+        return fail(h, PB_ERR_INVALID_ARG, "negative dimension or nnz");
+    if (A->ncols != B->nrows) return fail(h, PB_ERR_SHAPE, "A.ncols != B.nrows");
+    if (A->nnz > 0x7fffffffll || B->nnz > 0x7fffffffll)
+        return fail(h, PB_ERR_UNSUPPORTED, "operand nnz must fit int32 pointers");
+    if (!A->colptr || !B->rowptr) return fail(h, PB_ERR_INVALID_ARG, "pointer arrays must not be NULL");
+    if ((A->nnz > 0 && (!A->rowidx || !A->val)) || (B->nnz > 0 && (!B->colidx || !B->val)))
+        return fail(h, PB_ERR_INVALID_ARG, "index/value arrays must not be NULL when nnz > 0");
+    return PB_OK;
+}
+
+void free_plan_memory(pb_plan *p) {
+    if (!p || !p->h) return;
+    if (p->chunk_mem) p->h->free_fn(p->chunk_mem, p->chunk_bytes, nullptr, p->h->ctx);
+    if (p->arena) p->h->free_fn(p->arena, p->arena_bytes, nullptr, p->h->ctx);
+    p->chunk_mem = p->arena = nullptr;
+}
+
+}  // namespace
+
+extern "C" {
+
+int32_t pb_version(void) { return kVersion; }
+
+pb_status pb_create(pb_handle **out) {
+    if (!out) return PB_ERR_INVALID_ARG;
+    *out = nullptr;
+    pb_handle *h = new (std::nothrow) pb_handle();
+    if (!h) return PB_ERR_OOM;
+    cudaError_t e = cudaGetDevice(&h->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
+    if (e != cudaSuccess) {
+        delete h;
+        (void)cudaGetLastError();
+        return PB_ERR_CUDA;
+    }
+    h->alloc = default_alloc;
+    h->free_fn = default_free;
+    *out = h;
+    return PB_OK;
+}
+
+pb_status pb_destroy(pb_handle *h) {
+    delete h;
+    return PB_OK;
+}
+
+pb_status pb_set_allocator(pb_handle *h, pb_alloc_fn alloc, pb_free_fn free_fn, void *ctx) {
+    if (!h) return PB_ERR_INVALID_ARG;
+    if (alloc && !free_fn) return fail(h, PB_ERR_INVALID_ARG, "free_fn required with alloc");
+    h->alloc = alloc ? alloc : default_alloc;
+    h->free_fn = alloc ? free_fn : default_free;
+    h->ctx = alloc ? ctx : nullptr;
+    return PB_OK;
+}
+
+const char *pb_last_error(const pb_handle *h) { return h ? h->last_error.c_str() : "null handle"; }
+
+pb_status pb_spgemm_symbolic(pb_handle *h, const pb_csc *A, const pb_csr *B, pb_dtype dtype,
+                             const pb_config *cfg, pb_stream_t stream_, pb_plan **out) {
+    if (!h || !out) return PB_ERR_INVALID_ARG;
+    *out = nullptr;
+    h->last_error.clear();
+    pb_status st = check_operands(h, A, B);
+    if (st != PB_OK) return st;
+    if (!valid_dtype(dtype)) return fail(h, PB_ERR_UNSUPPORTED_DTYPE, "unknown dtype");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream_);
+
+    pb_plan *p = new (std::nothrow) pb_plan();
+    if (!p) return fail(h, PB_ERR_OOM, "host allocation failed");
+    p->h = h;
+    p->m = A->nrows;
+    p->k = A->ncols;
+    p->n = B->ncols;
+    p->nnzA = A->nnz;
+    p->nnzB = B->nnz;
+    p->dtype = dtype;
+    p->colbits = ceil_log2_u64((uint64_t)(p->n > 1 ? p->n : 2));
+    if (p->colbits > 31) {
+        delete p;
+        return fail(h, PB_ERR_UNSUPPORTED, "B.ncols too large for a 32-bit key");
+    }
+    int rowbits = 32 - p->colbits;
+    p->rmax_log2 = rowbits < 12 ? rowbits : 12;
+    if (cfg && cfg->bin_capacity) p->capacity = cfg->bin_capacity;
+    if (p->capacity != 2048 && p->capacity != 4096 && p->capacity != 8192) {
+        delete p;
+        return fail(h, PB_ERR_INVALID_ARG, "bin_capacity must be 2048, 4096 or 8192");
+    }
+    p->heavy = p->capacity / 2;
+    if (cfg && cfg->expand_chunk) {
+        if (cfg->expand_chunk < 32 || cfg->expand_chunk % 32) {
+            delete p;
+            return fail(h, PB_ERR_INVALID_ARG, "expand_chunk must be a positive multiple of 32");
+        }
+        p->chunk = cfg->expand_chunk;
+    }
+
+    // Arena of plan arrays.
+    const int64_t m = p->m, k = p->k;
+    const int64_t scan_n = (m > k ? m : k) + 2;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t o = off;
+        off += align256(bytes);
+        return o;
+    };
+    const size_t oF = take(8 * (k + 1)), oR = take(8 * (m + 1)), oFl = take(8 * (m + 1));
+    const size_t oRi = take(8 * (m > 0 ? m : 1)), oBr = take(4 * (m + 2)), oBo = take(8 * (m + 2));
+    const size_t oH = take(sizeof(PlanHeader)), oT = take(8 * scan_tmp_elems(scan_n)), oE = take(64);
+    p->arena_bytes = off;
+    p->arena = h->alloc(p->arena_bytes, stream_, h->ctx);
+    if (!p->arena) {
+        delete p;
+        return fail(h, PB_ERR_OOM, "plan allocation failed");
+    }
+    char *base = static_cast<char *>(p->arena);
+    p->F = reinterpret_cast<int64_t *>(base + oF);
+    p->R = reinterpret_cast<int64_t *>(base + oR);
+    p->flags = reinterpret_cast<int64_t *>(base + oFl);
+    p->rowinfo = reinterpret_cast<uint64_t *>(base + oRi);
+    p->bin_row = reinterpret_cast<int32_t *>(base + oBr);
+    p->bin_off = reinterpret_cast<int64_t *>(base + oBo);
+    p->dhdr = reinterpret_cast<PlanHeader *>(base + oH);
+    p->scan_tmp = reinterpret_cast<int64_t *>(base + oT);
+    p->err = reinterpret_cast<uint32_t *>(base + oE);
+
+    auto bail = [&](pb_status code) {
+        free_plan_memory(p);
+        delete p;
+        return code;
+    };
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(p->dhdr, 0, sizeof(PlanHeader), s)) != cudaSuccess ||
+        (e = cudaMemsetAsync(p->err, 0, 64, s)) != cudaSuccess) {
+        cuda_fail(h, e, "memset");
+        return bail(PB_ERR_CUDA);
+    }
+    SymbolicArgs a{};
+    a.m = p->m;
+    a.k = p->k;
+    a.n = p->n;
+    a.colptrA = A->colptr;
+    a.rowidxA = A->rowidx;
+    a.rowptrB = B->rowptr;
+    a.F = p->F;
+    a.R = p->R;
+    a.flags = p->flags;
+    a.rowinfo = p->rowinfo;
+    a.bin_row = p->bin_row;
+    a.bin_off = p->bin_off;
+    a.hdr = p->dhdr;
+    a.colbits = p->colbits;
+    a.rmax_log2 = p->rmax_log2;
+    a.capacity = p->capacity;
+    a.heavy = p->heavy;
+    if ((e = launch_symbolic(a, p->scan_tmp, s)) != cudaSuccess) {
+        cuda_fail(h, e, "symbolic launch");
+        return bail(PB_ERR_CUDA);
+    }
+    // The one synchronisation of the symbolic phase: read the sizes back.
+    if ((e = cudaMemcpyAsync(&p->hdr, p->dhdr, sizeof(PlanHeader), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(s)) != cudaSuccess) {
+        cuda_fail(h, e, "symbolic readback");
+        return bail(PB_ERR_CUDA);
+    }
+    if (p->hdr.n_oversize > 0) {
+        char msg[200];
+        snprintf(msg, sizeof msg, "%lld bin(s) exceed the on-chip capacity of %d tuples (largest %llu)",
+                 (long long)p->hdr.n_oversize, p->capacity, (unsigned long long)p->hdr.max_bin_count);
+        fail(h, PB_ERR_UNSUPPORTED, msg);
+        return bail(PB_ERR_UNSUPPORTED);
+    }
+    // Expand work items.
+    p->nchunks = ceil_div<int64_t>(p->hdr.flop, p->chunk);
+    if (p->nchunks > 0) {
+        p->chunk_bytes = align256(4 * (size_t)p->nchunks);
+        p->chunk_mem = h->alloc(p->chunk_bytes, stream_, h->ctx);
+        if (!p->chunk_mem) {
+            fail(h, PB_ERR_OOM, "chunk table allocation failed");
+            return bail(PB_ERR_OOM);
+        }
+        p->chunk_k = static_cast<int32_t *>(p->chunk_mem);
+        if ((e = launch_chunk_table(p->F, p->k, p->hdr.flop, p->chunk, p->chunk_k, s)) != cudaSuccess) {
+            cuda_fail(h, e, "chunk table");
+            return bail(PB_ERR_CUDA);
+        }
+    }
+    // Workspace layout of the numeric phase.
+    const size_t T = (size_t)p->hdr.tuples_padded;
+    const size_t nb = (size_t)p->hdr.nbins;
+    size_t w = 0;
+    p->ws_keys = w;
+    w += align256(4 * T);
+    p->ws_vals = w;
+    w += align256(tuple_val_bytes(dtype) * T);
+    p->ws_cursor = w;
+    w += align256(4 * nb);
+    p->ws_status = w;
+    w += align256(8 * nb);
+    p->ws_ctrl = w;
+    w += 256;
+    p->ws_bytes = w;
+    *out = p;
+    return PB_OK;
+}
+
+pb_status pb_plan_query(const pb_plan *p, int64_t *flop, int64_t *c_cap, size_t *workspace_bytes, int64_t *nbins,
+                        int32_t *npanels) {
+    if (!p) return PB_ERR_INVALID_ARG;
+    if (flop) *flop = p->hdr.flop;
+    if (c_cap) *c_cap = p->hdr.flop;
+    if (workspace_bytes) *workspace_bytes = p->ws_bytes;
+    if (nbins) *nbins = p->hdr.nbins;
+    if (npanels) *npanels = 1;
+    return PB_OK;
+}
+
+static pb_status fill_numeric(pb_handle *h, const pb_plan *p, const pb_csc *A, const pb_csr *B, void *workspace,
+                              size_t ws_bytes, NumericArgs &a) {
+    pb_status st = check_operands(h, A, B);
+    if (st != PB_OK) return st;
+    if (A->nrows != p->m || A->ncols != p->k || B->ncols != p->n || A->nnz != p->nnzA || B->nnz != p->nnzB)
+        return fail(h, PB_ERR_SHAPE, "operands differ from the planned structure");
+    if (!workspace && p->ws_bytes) return fail(h, PB_ERR_INVALID_ARG, "workspace must not be NULL");
+    if (ws_bytes < p->ws_bytes) return fail(h, PB_ERR_WORKSPACE, "workspace smaller than pb_plan_query reported");
+    if (reinterpret_cast<uintptr_t>(workspace) & 255)
+        return fail(h, PB_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
+    char *w = static_cast<char *>(workspace);
+    a = NumericArgs{};
+    a.m = p->m;
+    a.k = p->k;
+    a.n = p->n;
+    a.colptrA = A->colptr;
+    a.rowidxA = A->rowidx;
+    a.rowptrB = B->rowptr;
+    a.colidxB = B->colidx;
+    a.valA = A->val;
+    a.valB = B->val;
+    a.F = p->F;
+    a.R = p->R;
+    a.rowinfo = p->rowinfo;
+    a.bin_row = p->bin_row;
+    a.bin_off = p->bin_off;
+    a.chunk_k = p->chunk_k;
+    a.flop = p->hdr.flop;
+    a.nbins = p->hdr.nbins;
+    a.nchunks = p->nchunks;
+    a.chunk = p->chunk;
+    a.colbits = p->colbits;
+    a.capacity = p->capacity;
+    a.keys = reinterpret_cast<uint32_t *>(w + p->ws_keys);
+    a.vals = w + p->ws_vals;
+    a.cursor = reinterpret_cast<uint32_t *>(w + p->ws_cursor);
+    a.status = reinterpret_cast<uint64_t *>(w + p->ws_status);
+    a.ticket = reinterpret_cast<uint32_t *>(w + p->ws_ctrl);
+    a.err = p->err;
+    a.dtype = p->dtype;
+    a.num_sms = h->num_sms;
+    return PB_OK;
+}
+
+pb_status pb_spgemm_numeric(pb_handle *h, const pb_plan *p, const pb_csc *A, const pb_csr *B, pb_csr_out *C,
+                            void *workspace, size_t ws_bytes, pb_stream_t stream_) {
+    if (!h || !p || !C) return PB_ERR_INVALID_ARG;
+    h->last_error.clear();
+    NumericArgs a;
+    pb_status st = fill_numeric(h, p, A, B, workspace, ws_bytes, a);
+    if (st != PB_OK) return st;
+    if (C->nrows != p->m || C->ncols != p->n) return fail(h, PB_ERR_SHAPE, "C must be A.nrows x B.ncols");
+    if ((C->rowptr64 == nullptr) == (C->rowptr32 == nullptr))
+        return fail(h, PB_ERR_INVALID_ARG, "exactly one of C.rowptr64 / C.rowptr32 must be set");
+    if (C->cap < 0 || (C->cap > 0 && (!C->colidx || !C->val)))
+        return fail(h, PB_ERR_INVALID_ARG, "C arrays must not be NULL when cap > 0");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream_);
+    a.rowptr64 = C->rowptr64;
+    a.rowptr32 = C->rowptr32;
+    a.colidx = C->colidx;
+    a.valC = C->val;
+    a.nnz_dev = C->nnz_dev;
+    a.cap = C->cap;
+    const size_t nb = (size_t)p->hdr.nbins;
+    char *w = static_cast<char *>(workspace);
+    if (h->phase_on) PB_CUDA(h, cudaEventRecord(h->phase_ev[0], s));
+    PB_CUDA(h, cudaMemsetAsync(p->err, 0, 4, s));
+    if (p->m == 0) {
+        // no rows: C is the empty matrix with rowptr = [0]
+        if (C->rowptr64) PB_CUDA(h, cudaMemsetAsync(C->rowptr64, 0, 8, s));
+        if (C->rowptr32) PB_CUDA(h, cudaMemsetAsync(C->rowptr32, 0, 4, s));
+        if (C->nnz_dev) PB_CUDA(h, cudaMemsetAsync(C->nnz_dev, 0, 8, s));
+        return PB_OK;
+    }
+    PB_CUDA(h, cudaMemsetAsync(w + p->ws_cursor, 0, 4 * nb, s));
+    PB_CUDA(h, cudaMemsetAsync(w + p->ws_status, 0, 8 * nb, s));
+    PB_CUDA(h, cudaMemsetAsync(w + p->ws_ctrl, 0, 256, s));
+    if (h->phase_on) PB_CUDA(h, cudaEventRecord(h->phase_ev[1], s));
+    PB_CUDA(h, launch_expand(a, s));
+    if (h->phase_on) PB_CUDA(h, cudaEventRecord(h->phase_ev[2], s));
+    PB_CUDA(h, launch_binsort(a, s));
+    if (h->phase_on) PB_CUDA(h, cudaEventRecord(h->phase_ev[3], s));
+    return PB_OK;
+}
+
+pb_status pb_set_phase_events(pb_handle *h, void *const *events) {
+    if (!h) return PB_ERR_INVALID_ARG;
+    h->phase_on = events != nullptr;
+    for (int i = 0; i < 4; ++i) h->phase_ev[i] = events ? static_cast<cudaEvent_t>(events[i]) : nullptr;
+    if (events)
+        for (int i = 0; i < 4; ++i)
+            if (!h->phase_ev[i]) {
+                h->phase_on = false;
+                return fail(h, PB_ERR_INVALID_ARG, "all four events are required");
+            }
+    return PB_OK;
+}
+
+int64_t pb_kernel_launches(void) { return pb::g_launches.load(); }
+
+pb_status pb_debug_expand(pb_handle *h, const pb_plan *p, const pb_csc *A, const pb_csr *B, void *workspace,
+                          size_t ws_bytes, pb_stream_t stream_) {
+    if (!h || !p) return PB_ERR_INVALID_ARG;
+    NumericArgs a;
+    pb_status st = fill_numeric(h, p, A, B, workspace, ws_bytes, a);
+    if (st != PB_OK) return st;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream_);
+    char *w = static_cast<char *>(workspace);
+    PB_CUDA(h, cudaMemsetAsync(w + p->ws_cursor, 0, 4 * (size_t)p->hdr.nbins, s));
+    PB_CUDA(h, launch_expand(a, s));
+    return PB_OK;
+}
+
+size_t pb_debug_values_offset(const pb_plan *p) { return p ? p->ws_vals : 0; }
+
+pb_status pb_plan_status(const pb_plan *p, pb_stream_t stream_, pb_status *device_status) {
+    if (!p || !device_status) return PB_ERR_INVALID_ARG;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream_);
+    uint32_t word = 0;
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = cudaMemcpy(&word, p->err, 4, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(p->h, e, "plan status");
+    if (word & DEV_ERR_OVERFLOW)
+        *device_status = PB_ERR_OVERFLOW;
+    else if (word & DEV_ERR_TIMEOUT)
+        *device_status = PB_ERR_TIMEOUT;
+    else if (word & DEV_ERR_CAPACITY)
+        *device_status = PB_ERR_UNSUPPORTED;
+    else
+        *device_status = PB_OK;
+    return PB_OK;
+}
+
+pb_status pb_plan_export(const pb_plan *p, int64_t *F, int64_t *R, int32_t *bin_row, int64_t *bin_off,
+                         pb_stream_t stream_) {
+    if (!p) return PB_ERR_INVALID_ARG;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream_);
+    pb_handle *h = p->h;
+    const size_t nb = (size_t)p->hdr.nbins;
+    if (F) PB_CUDA(h, cudaMemcpyAsync(F, p->F, 8 * ((size_t)p->k + 1), cudaMemcpyDeviceToDevice, s));
+    if (R) PB_CUDA(h, cudaMemcpyAsync(R, p->R, 8 * ((size_t)p->m + 1), cudaMemcpyDeviceToDevice, s));
+    if (bin_row) PB_CUDA(h, cudaMemcpyAsync(bin_row, p->bin_row, 4 * (nb + 1), cudaMemcpyDeviceToDevice, s));
+    if (bin_off) PB_CUDA(h, cudaMemcpyAsync(bin_off, p->bin_off, 8 * (nb + 1), cudaMemcpyDeviceToDevice, s));
+    PB_CUDA(h, cudaStreamSynchronize(s));
+    return PB_OK;
+}
+
+pb_status pb_plan_destroy(pb_plan *p) {
+    if (!p) return PB_OK;
+    free_plan_memory(p);
+    delete p;
+    return PB_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,221 @@
+// Internal definitions shared by the CUDA translation units of libpbspgemm.
+// Nothing here is part of the public ABI (include/pb_spgemm.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "pb_spgemm.h"
+
+namespace pb {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+// Device status word bits (pb_plan_status maps the lowest set bit to a pb_status).
+enum : uint32_t {
+    DEV_ERR_OVERFLOW = 1u << 0,   // nnz(C) > C.cap or an int32 row pointer would overflow
+    DEV_ERR_TIMEOUT = 1u << 1,    // a bounded wait (look-back, mbarrier) gave up
+    DEV_ERR_CAPACITY = 1u << 2,   // a bin held more tuples than the plan sized it for
+};
+
+// Look-back status of one bin: two flag bits over a 62-bit count.
+constexpr uint64_t LB_FLAG_SHIFT = 62;
+constexpr uint64_t LB_AGGREGATE = 1ull << LB_FLAG_SHIFT;
+constexpr uint64_t LB_PREFIX = 2ull << LB_FLAG_SHIFT;
+constexpr uint64_t LB_VALUE_MASK = (1ull << LB_FLAG_SHIFT) - 1;
+
+// Bounded spin: every device wait gives up after this many polls.
+constexpr uint32_t SPIN_LIMIT = 1u << 24;
+
+// Plan header filled on the device by the symbolic phase, read back once.
+struct PlanHeader {
+    int64_t flop;
+    int64_t nbins;
+    int64_t tuples_padded;   // sum over bins of round_up(count, 4)
+    unsigned long long max_bin_count;
+    unsigned long long max_light_row;  // largest per-row flop among rows <= heavy threshold
+    int64_t n_oversize;      // bins holding more than bin_capacity tuples
+    int64_t pad[2];
+};
+
+// Arguments of the kernels (passed by value).
+struct SymbolicArgs {
+    int32_t m, k, n;
+    const int32_t *colptrA, *rowidxA, *rowptrB;
+    int64_t *F;          // [k+1]
+    int64_t *R;          // [m+1]
+    int64_t *flags;      // [m+1] scratch: bin-start flags, then their exclusive scan
+    uint64_t *rowinfo;   // [m]   (bin << 32) | (local_row << colbits)
+    int32_t *bin_row;    // [m+2]
+    int64_t *bin_off;    // [m+2]
+    PlanHeader *hdr;
+    int32_t colbits, rmax_log2;
+    int64_t capacity, heavy;
+};
+
+template <class T>
+__host__ __device__ inline T ceil_div(T a, T b) { return (a + b - 1) / b; }
+
+__device__ inline uint32_t lanemask_lt() {
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+__device__ inline void st_release_u64(uint64_t *p, uint64_t v) {
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ inline uint64_t ld_acquire_u64(const uint64_t *p) {
+    uint64_t v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// ---------------------------------------------------------------------------
+// mbarrier + bulk copy (TMA, non-tensor form) helpers.
+// ---------------------------------------------------------------------------
+__device__ inline uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ inline void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ inline void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ inline bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait on an mbarrier phase.  Returns false on timeout.
+__device__ inline bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
+    for (uint32_t it = 0; it < SPIN_LIMIT; ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+    }
+    return false;
+}
+
+// Order this thread's earlier generic-proxy shared-memory accesses before
+// later async-proxy (bulk copy) accesses of the same CTA.
+__device__ inline void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// Global -> shared bulk copy completing on `bar`.  dst, src 16-byte aligned,
+// bytes a multiple of 16.
+__device__ inline void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// ---------------------------------------------------------------------------
+// Block-wide scans.
+// ---------------------------------------------------------------------------
+template <class T>
+__device__ inline T warp_inclusive_scan(T v) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        T t = __shfl_up_sync(FULL, v, o);
+        if (lane >= o) v += t;
+    }
+    return v;
+}
+
+// Exclusive scan of one value per thread over the block; returns the prefix,
+// writes the block total to *total.  `scratch` holds >= 33 elements.
+template <class T, int THREADS>
+__device__ inline T block_exclusive_scan(T v, T *scratch, T *total) {
+    constexpr int NW = THREADS / 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    T inc = warp_inclusive_scan(v);
+    if (lane == 31) scratch[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        T w = (lane < NW) ? scratch[lane] : T(0);
+        T wi = warp_inclusive_scan(w);
+        if (lane < NW) scratch[lane] = wi - w;
+        if (lane == NW - 1) scratch[32] = wi;
+    }
+    __syncthreads();
+    T res = scratch[warp] + inc - v;
+    *total = scratch[32];
+    __syncthreads();
+    return res;
+}
+
+template <class T, int THREADS>
+__device__ inline T block_reduce_sum(T v, T *scratch) {
+    T total;
+    (void)block_exclusive_scan<T, THREADS>(v, scratch, &total);
+    return total;
+}
+
+// Host-side launch of the device-wide int64 exclusive scan (pb_scan.cu).
+// Scans x[0..n) in place and writes the total to x[n].  tmp must hold
+// scan_tmp_elems(n) int64 elements.
+int64_t scan_tmp_elems(int64_t n);
+cudaError_t scan_i64(int64_t *x, int64_t n, int64_t *tmp, cudaStream_t s);
+
+// Process-wide count of kernels launched by the library (pb_kernel_launches).
+void count_launches(int64_t n);
+
+// Kernel launchers implemented in the other translation units.
+cudaError_t launch_symbolic(const SymbolicArgs &a, int64_t *scan_tmp, cudaStream_t s);
+cudaError_t launch_chunk_table(const int64_t *F, int32_t k, int64_t flop, int64_t chunk, int32_t *chunk_k,
+                               cudaStream_t s);
+
+struct NumericArgs {
+    // inputs
+    int32_t m, k, n;
+    const int32_t *colptrA, *rowidxA, *rowptrB, *colidxB;
+    const void *valA, *valB;
+    // plan
+    const int64_t *F, *R;
+    const uint64_t *rowinfo;
+    const int32_t *bin_row;
+    const int64_t *bin_off;
+    const int32_t *chunk_k;
+    int64_t flop, nbins, nchunks, chunk;
+    int32_t colbits;
+    int32_t capacity;
+    // workspace
+    uint32_t *keys;
+    void *vals;
+    uint32_t *cursor;    // [nbins]
+    uint64_t *status;    // [nbins] look-back words
+    uint32_t *ticket;    // [1]
+    uint32_t *err;       // [1] device status word
+    // output
+    int64_t *rowptr64;
+    int32_t *rowptr32;
+    int32_t *colidx;
+    void *valC;
+    int64_t *nnz_dev;
+    int64_t cap;
+    int dtype;
+    int num_sms;
+};
+
+cudaError_t launch_expand(const NumericArgs &a, cudaStream_t s);
+cudaError_t launch_binsort(const NumericArgs &a, cudaStream_t s);
+int binsort_max_capacity(int dtype);
+
+}  // namespace pb

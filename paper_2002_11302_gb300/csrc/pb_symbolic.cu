@@ -1,0 +1,177 @@
+// Symbolic phase (Alg. 3, Sec. III-B): flop counts and row-range bins.
+//
+//  1. f_k = nnz(A(:,k)) * nnz(B(k,:)) and its prefix F (Alg. 3).
+//  2. Per-row flop r_i = sum over A(i,k) != 0 of nnz(B(k,:)) (the per-row form
+//     of Alg. 3 in Sec. III-B) and its prefix R.
+//  3. Rows are cut into bins of consecutive rows (the row ranges of Fig. 4 and
+//     the "variable ranges of rows" of Sec. III-D).  A bin starts at row i when
+//       i is a multiple of 2^rmax_log2 (keeps the in-bin row offset small),
+//       R[i] and R[i-1] fall in different windows of width T, or
+//       row i or row i-1 is heavy (r > heavy threshold H).
+//     Light bins therefore hold fewer than T + max_light_row tuples; T is
+//     chosen as capacity - max_light_row so they fit the on-chip sort.  A
+//     heavy row is a bin of its own.
+//  4. Bin offsets: counts padded to a multiple of 4 tuples (16-byte aligned
+//     key segments for the bulk copies of the sort phase) and prefix-summed.
+#include "pb_common.cuh"
+
+namespace pb {
+
+namespace {
+
+__global__ void k_flop_per_k(int32_t k, const int32_t *colptrA, const int32_t *rowptrB, int64_t *F) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < k; i += (int64_t)gridDim.x * blockDim.x) {
+        int64_t la = (int64_t)colptrA[i + 1] - colptrA[i];
+        int64_t lb = (int64_t)rowptrB[i + 1] - rowptrB[i];
+        F[i] = la * lb;
+    }
+}
+
+// One warp per column k: every A(i,k) adds nnz(B(k,:)) to row i.
+__global__ void k_row_flop(int32_t k, const int32_t *colptrA, const int32_t *rowidxA, const int32_t *rowptrB,
+                           int64_t *R) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t col = warp; col < k; col += nwarps) {
+        const int32_t a0 = colptrA[col], a1 = colptrA[col + 1];
+        const int64_t lb = (int64_t)rowptrB[col + 1] - rowptrB[col];
+        if (lb == 0) continue;
+        for (int32_t e = a0 + lane; e < a1; e += 32)
+            atomicAdd(reinterpret_cast<unsigned long long *>(&R[rowidxA[e]]), (unsigned long long)lb);
+    }
+}
+
+__global__ void k_max_light(int32_t m, const int64_t *R, int64_t heavy, PlanHeader *hdr) {
+    unsigned long long best = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+        int64_t r = R[i + 1] - R[i];
+        if (r <= heavy && (unsigned long long)r > best) best = (unsigned long long)r;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        unsigned long long t = __shfl_down_sync(FULL, best, o);
+        best = t > best ? t : best;
+    }
+    if ((threadIdx.x & 31) == 0 && best) atomicMax(&hdr->max_light_row, best);
+}
+
+__device__ inline bool is_heavy(const int64_t *R, int64_t i, int64_t heavy) { return R[i + 1] - R[i] > heavy; }
+
+__global__ void k_bin_flags(int32_t m, const int64_t *R, int64_t capacity, int64_t heavy, int32_t rmax_log2,
+                            const PlanHeader *hdr, int64_t *flags) {
+    const int64_t T = capacity - (int64_t)hdr->max_light_row;  // >= capacity - heavy > 0
+    const int64_t rmask = (1ll << rmax_log2) - 1;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+        bool start = (i == 0) || ((i & rmask) == 0);
+        if (!start) {
+            start = (R[i] / T) != (R[i - 1] / T) || is_heavy(R, i, heavy) || is_heavy(R, i - 1, heavy);
+        }
+        flags[i] = start ? 1 : 0;
+    }
+}
+
+// flags now holds the exclusive scan of the start flags; flags[m] = nbins.
+__global__ void k_bin_rows(int32_t m, const int64_t *scanned, int32_t *bin_row, PlanHeader *hdr) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t next = (i + 1 < m) ? scanned[i + 1] : scanned[m];
+        if (next != scanned[i]) bin_row[scanned[i]] = (int32_t)i;  // row i starts bin scanned[i]
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        bin_row[scanned[m]] = m;
+        hdr->nbins = scanned[m];
+    }
+}
+
+__global__ void k_rowinfo(int32_t m, const int64_t *scanned, const int32_t *bin_row, int32_t colbits,
+                          uint64_t *rowinfo) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t next = (i + 1 < m) ? scanned[i + 1] : scanned[m];
+        const int64_t bin = (next != scanned[i]) ? scanned[i] : scanned[i] - 1;
+        const uint32_t local = (uint32_t)(i - bin_row[bin]);
+        rowinfo[i] = ((uint64_t)bin << 32) | (uint64_t)(local << colbits);
+    }
+}
+
+__global__ void k_bin_sizes(const int64_t *R, const int32_t *bin_row, int64_t capacity, PlanHeader *hdr,
+                            int64_t *bin_off) {
+    const int64_t nbins = hdr->nbins;
+    unsigned long long mx = 0;
+    long long over = 0;
+    for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < nbins; b += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t cnt = R[bin_row[b + 1]] - R[bin_row[b]];
+        bin_off[b] = (cnt + 3) & ~int64_t(3);
+        if ((unsigned long long)cnt > mx) mx = cnt;
+        if (cnt > capacity) ++over;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        unsigned long long t = __shfl_down_sync(FULL, mx, o);
+        mx = t > mx ? t : mx;
+        over += __shfl_down_sync(FULL, over, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (mx) atomicMax(&hdr->max_bin_count, mx);
+        if (over) atomicAdd(reinterpret_cast<unsigned long long *>(&hdr->n_oversize), (unsigned long long)over);
+    }
+}
+
+__global__ void k_finish_header(const int64_t *F, int32_t k, const int64_t *bin_off, PlanHeader *hdr) {
+    hdr->flop = F[k];
+    hdr->tuples_padded = bin_off[hdr->nbins];
+}
+
+// Chunk table for the expand phase: chunk c starts at tuple c*chunk, which
+// lies in column k with F[k] <= c*chunk < F[k+1].
+__global__ void k_chunk_table(const int64_t *F, int32_t k, int64_t flop, int64_t chunk, int32_t *chunk_k) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < k; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t lo = F[i], hi = F[i + 1];
+        if (hi <= lo) continue;
+        for (int64_t c = ceil_div<int64_t>(lo, chunk); c * chunk < hi && c * chunk < flop; ++c) chunk_k[c] = (int32_t)i;
+    }
+}
+
+unsigned grid_for(int64_t n, int threads) {
+    int64_t g = ceil_div<int64_t>(n > 0 ? n : 1, threads);
+    if (g > 65535ll * 32) g = 65535ll * 32;
+    return (unsigned)g;
+}
+
+}  // namespace
+
+cudaError_t launch_symbolic(const SymbolicArgs &a, int64_t *scan_tmp, cudaStream_t s) {
+    cudaError_t e;
+    const int T = 256;
+    // 1. per-k flop and its prefix (Alg. 3)
+    k_flop_per_k<<<grid_for(a.k, T), T, 0, s>>>(a.k, a.colptrA, a.rowptrB, a.F);
+    if ((e = scan_i64(a.F, a.k, scan_tmp, s)) != cudaSuccess) return e;
+    // 2. per-row flop (Sec. III-B) and its prefix
+    if ((e = cudaMemsetAsync(a.R, 0, sizeof(int64_t) * ((size_t)a.m + 1), s)) != cudaSuccess) return e;
+    k_row_flop<<<grid_for((int64_t)a.k * 32, T), T, 0, s>>>(a.k, a.colptrA, a.rowidxA, a.rowptrB, a.R);
+    if ((e = scan_i64(a.R, a.m, scan_tmp, s)) != cudaSuccess) return e;
+    // 3. bins
+    k_max_light<<<grid_for(a.m, T), T, 0, s>>>(a.m, a.R, a.heavy, a.hdr);
+    k_bin_flags<<<grid_for(a.m, T), T, 0, s>>>(a.m, a.R, a.capacity, a.heavy, a.rmax_log2, a.hdr, a.flags);
+    if ((e = scan_i64(a.flags, a.m, scan_tmp, s)) != cudaSuccess) return e;
+    k_bin_rows<<<grid_for(a.m, T), T, 0, s>>>(a.m, a.flags, a.bin_row, a.hdr);
+    k_rowinfo<<<grid_for(a.m, T), T, 0, s>>>(a.m, a.flags, a.bin_row, a.colbits, a.rowinfo);
+    // 4. bin sizes and offsets.  The bin count lives on the device, so the
+    //    offsets are scanned over the m-entry upper bound: entries past nbins
+    //    stay zero and bin_off[nbins] receives the total.
+    if ((e = cudaMemsetAsync(a.bin_off, 0, sizeof(int64_t) * ((size_t)a.m + 2), s)) != cudaSuccess) return e;
+    k_bin_sizes<<<grid_for(a.m, T), T, 0, s>>>(a.R, a.bin_row, a.capacity, a.hdr, a.bin_off);
+    if ((e = scan_i64(a.bin_off, a.m, scan_tmp, s)) != cudaSuccess) return e;
+    k_finish_header<<<1, 1, 0, s>>>(a.F, a.k, a.bin_off, a.hdr);
+    count_launches(8);  // the non-scan kernels above
+    return cudaGetLastError();
+}
+
+cudaError_t launch_chunk_table(const int64_t *F, int32_t k, int64_t flop, int64_t chunk, int32_t *chunk_k,
+                               cudaStream_t s) {
+    if (flop <= 0) return cudaSuccess;
+    k_chunk_table<<<grid_for(k, 256), 256, 0, s>>>(F, k, flop, chunk, chunk_k);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+}  // namespace pb

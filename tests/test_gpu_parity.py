@@ -1,0 +1,243 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Structure (row pointers, column indices) must match bit-exactly; values must be
+within 64 * eps * sum_k |a_ik b_kj| per entry (eps = 2^-53 for FP64, 2^-24
+when products are rounded to FP32).  Inputs are seeded synthetic matrices.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from helpers import EPS, assert_csr_valid, assert_matches, assert_rows_match
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pb():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2002_11302_gb300 import binding
+    binding.load_library()
+    return binding
+
+
+def run(pb, A, B, dtype=0, cap=0, rowptr64=True, vdt=None):
+    Ad = pb.csc_to_device(A, val_dtype=vdt)
+    Bd = pb.csr_to_device(B, val_dtype=vdt)
+    cfg = pb.make_config(bin_capacity=cap) if cap else None
+    return pb.spgemm(Ad, Bd, dtype=dtype, config=cfg, rowptr64=rowptr64)
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_tiny_random_rectangular(pb, seed):
+    rng = np.random.default_rng(seed)
+    m, k, n = (int(x) for x in rng.integers(1, 70, 3))
+    dens = float(rng.uniform(0.01, 0.6))
+    A, _ = synth.random_sparse(m, k, dens, seed=10 + seed)
+    _, B = synth.random_sparse(k, n, dens, seed=20 + seed)
+    C = run(pb, A, B)
+    assert_matches(C, oracle.spgemm(A, B), EPS["f64"])
+
+
+def test_er_4096_d4(pb):
+    A, B = synth.er(4096, 4, seed=0)
+    C = run(pb, A, B)
+    ref = oracle.spgemm(A, B)
+    assert_matches(C, ref, EPS["f64"])
+    assert ref.nnz <= oracle.flop(A, B)
+
+
+@pytest.mark.parametrize("cap", [2048, 4096, 8192])
+@pytest.mark.parametrize("n,d", [(20000, 8), (3000, 16), (50000, 2), (1 << 15, 5)])
+def test_er_capacities(pb, n, d, cap):
+    A, B = synth.er(n, d, seed=n + d, shuffle_within=True)
+    C = run(pb, A, B, cap=cap)
+    assert_matches(C, oracle.spgemm(A, B), EPS["f64"])
+
+
+def test_rmat_small_skewed(pb):
+    A, B = synth.rmat(11, 4, seed=2)
+    C = run(pb, A, B)
+    assert_matches(C, oracle.spgemm(A, B), EPS["f64"])
+
+
+def test_identity_and_permutation_bit_exact(pb):
+    A, B = synth.er(5000, 6, seed=3)
+    Ic, Ir = synth.identity(5000)
+    C = run(pb, Ic, B)
+    ref = oracle.spgemm(Ic, B)
+    assert_matches(C, ref, 0.0)             # one product per entry, times 1.0: exact
+    Pc, _, perm = synth.permutation(5000, seed=4)
+    C = run(pb, Pc, B)
+    assert_matches(C, oracle.spgemm(Pc, B), 0.0)
+    C = run(pb, A, Ir)
+    assert_matches(C, oracle.spgemm(A, Ir), 0.0)
+
+
+def test_amg_galerkin_chain_bit_exact(pb):
+    N = 8
+    A = synth.poisson7(N)
+    A_csc = synth.CSC(A.nrows, A.ncols, A.rowptr, A.colidx, A.val)
+    P = synth.aggregation_prolongator(N)
+    AP = run(pb, A_csc, P, rowptr64=False)
+    ref_AP = oracle.spgemm(A_csc, P)
+    assert_matches(AP, ref_AP, 0.0)          # integer values: exact
+    PT = synth.transpose_csr_as_csc(P)
+    APh = synth.CSR(A.nrows, P.ncols, AP.rowptr.cpu().numpy(), AP.colidx.cpu().numpy(), AP.val.cpu().numpy())
+    G = run(pb, PT, APh)
+    Gref = oracle.spgemm(PT, APh)
+    assert_matches(G, Gref, 0.0)
+    vals = G.val.cpu().numpy()
+    assert set(np.unique(vals).tolist()) <= {24.0, -4.0}
+
+
+def test_fp32_values(pb):
+    A, B = synth.er(20000, 6, seed=8, dtype=np.float32)
+    C = run(pb, A, B, dtype=pb.PB_F32)
+    ref = oracle.spgemm(A, B)               # FP64 oracle on the same (widened) inputs
+    assert C.val.dtype == torch.float32
+    assert_matches(C, ref, EPS["f32"])
+
+
+def test_fp32_tuples_fp64_merge(pb):
+    A, B = synth.er(30000, 8, seed=9)
+    C = run(pb, A, B, dtype=pb.PB_F64_F32TUPLE)
+    assert C.val.dtype == torch.float64
+    ref = oracle.spgemm(A, B)
+    assert_matches(C, ref, EPS["f32"])
+
+
+def test_int32_rowptr_output(pb):
+    A, B = synth.er(10000, 4, seed=12)
+    C = run(pb, A, B, rowptr64=False)
+    assert C.rowptr.dtype == torch.int32
+    assert_matches(C, oracle.spgemm(A, B), EPS["f64"])
+
+
+def test_degenerate_shapes(pb):
+    # empty columns of A, empty rows of B, rows with no products, a single row
+    A = synth.CSC(4, 3, np.array([0, 2, 2, 3], np.int32), np.array([0, 3, 1], np.int32), np.array([1.0, 2.0, 3.0]))
+    B = synth.CSR(3, 5, np.array([0, 2, 3, 3], np.int32), np.array([4, 0, 2], np.int32), np.array([5.0, 7.0, 9.0]))
+    C = run(pb, A, B)
+    assert_matches(C, oracle.spgemm(A, B), EPS["f64"])
+    # no products at all (flop = 0)
+    Z = synth.CSC(6, 3, np.zeros(4, np.int32), np.zeros(0, np.int32), np.zeros(0))
+    C = run(pb, Z, B)
+    assert C.rowptr.cpu().tolist() == [0] * 7
+    # one row, one column
+    A1 = synth.CSC(1, 1, np.array([0, 1], np.int32), np.array([0], np.int32), np.array([3.0]))
+    B1 = synth.CSR(1, 1, np.array([0, 1], np.int32), np.array([0], np.int32), np.array([-2.0]))
+    C = run(pb, A1, B1)
+    assert C.rowptr.cpu().tolist() == [0, 1] and C.val.cpu().tolist() == [-6.0]
+
+
+def test_empty_rows_span_many_bins(pb):
+    # a tall A whose rows are mostly empty: bins are cut at the in-bin row limit
+    A = synth.er_csc(300, 3, seed=5, nrows=200000)
+    _, B = synth.er(300, 7, seed=6)
+    C = run(pb, A, B)
+    assert_matches(C, oracle.spgemm(A, B), EPS["f64"])
+
+
+def test_symbolic_arrays_match_oracle(pb):
+    A, B = synth.er(40000, 7, seed=21, shuffle_within=True)
+    Ad, Bd = pb.csc_to_device(A), pb.csr_to_device(B)
+    plan = pb.symbolic(Ad, Bd)
+    F, R, bin_row, bin_off = (t.cpu().numpy() for t in plan.export())
+    assert plan.flop == oracle.flop(A, B) == 40000 * 49
+    la, lb = np.diff(A.colptr).astype(np.int64), np.diff(B.rowptr).astype(np.int64)
+    assert np.array_equal(F, np.concatenate([[0], np.cumsum(la * lb)]))           # Alg. 3 prefix
+    assert np.array_equal(np.diff(R), oracle.row_flop(A, B))                      # per-row flop
+    # bins: consecutive row ranges covering all rows, each within the on-chip capacity
+    assert bin_row[0] == 0 and bin_row[-1] == A.nrows and np.all(np.diff(bin_row) > 0)
+    counts = R[bin_row[1:]] - R[bin_row[:-1]]
+    assert counts.max() <= 4096
+    assert np.array_equal(np.diff(bin_off), (counts + 3) // 4 * 4)
+
+
+def test_expand_tuples_match_oracle_expansion(pb):
+    A, B = synth.er(6000, 6, seed=31, shuffle_within=True)
+    Ad, Bd = pb.csc_to_device(A), pb.csr_to_device(B)
+    plan = pb.symbolic(Ad, Bd)
+    ws = plan.workspace()
+    ws, voff = pb.debug_expand(plan, Ad, Bd, ws)
+    torch.cuda.synchronize()
+    _, R, bin_row, bin_off = (t.cpu().numpy() for t in plan.export())
+    wsh = ws.cpu().numpy()
+    keys = wsh[: 4 * int(bin_off[-1])].view(np.uint32)
+    vals = wsh[voff: voff + 8 * int(bin_off[-1])].view(np.float64)
+    colbits = max(1, int(np.ceil(np.log2(max(B.ncols, 2)))))
+    rows, cols, vs = [], [], []
+    for b in range(plan.nbins):
+        cnt = int(R[bin_row[b + 1]] - R[bin_row[b]])
+        k = keys[bin_off[b]: bin_off[b] + cnt]
+        r = bin_row[b] + (k >> colbits).astype(np.int64)
+        assert np.all(r < bin_row[b + 1]), "tuple outside its bin's row range"
+        rows.append(r)
+        cols.append((k & ((1 << colbits) - 1)).astype(np.int64))
+        vs.append(vals[bin_off[b]: bin_off[b] + cnt])
+    got = np.lexsort((np.concatenate(vs), np.concatenate(cols), np.concatenate(rows)))
+    er, ec, ev = oracle.expand(A, B)
+    exp = np.lexsort((ev, ec, er))
+    assert np.array_equal(np.concatenate(rows)[got], er[exp].astype(np.int64))
+    assert np.array_equal(np.concatenate(cols)[got], ec[exp].astype(np.int64))
+    assert np.array_equal(np.concatenate(vs)[got], ev[exp])       # one rounding each: bit-exact
+
+
+def test_capacity_overflow_reported(pb):
+    A, B = synth.er(5000, 4, seed=41)
+    Ad, Bd = pb.csc_to_device(A), pb.csr_to_device(B)
+    plan = pb.symbolic(Ad, Bd)
+    C = pb.alloc_output(plan, cap=100)
+    pb.numeric(plan, Ad, Bd, C, plan.workspace())
+    assert plan.status() == 5                # PB_ERR_OVERFLOW, nothing written past cap
+
+
+def test_workspace_too_small_rejected(pb):
+    A, B = synth.er(5000, 4, seed=42)
+    Ad, Bd = pb.csc_to_device(A), pb.csr_to_device(B)
+    plan = pb.symbolic(Ad, Bd)
+    C = pb.alloc_output(plan)
+    ws = torch.empty(plan.workspace_bytes // 2, dtype=torch.uint8, device="cuda")
+    with pytest.raises(pb.PBError) as ei:
+        pb.numeric(plan, Ad, Bd, C, ws)
+    assert ei.value.status == 10
+
+
+def test_shape_mismatch_rejected(pb):
+    A, _ = synth.er(100, 3, seed=1)
+    _, B = synth.er(101, 3, seed=1)
+    with pytest.raises(pb.PBError) as ei:
+        pb.symbolic(pb.csc_to_device(A), pb.csr_to_device(B))
+    assert ei.value.status == 2
+
+
+def test_plan_reuse_with_new_values(pb):
+    A, B = synth.er(8000, 5, seed=51)
+    Ad, Bd = pb.csc_to_device(A), pb.csr_to_device(B)
+    plan = pb.symbolic(Ad, Bd)
+    ws = plan.workspace()
+    for scale in (1.0, -3.5):
+        Ad.val.copy_(torch.from_numpy(A.val * scale))
+        C = pb.alloc_output(plan)
+        pb.numeric(plan, Ad, Bd, C, ws)
+        assert plan.status() == 0
+        A2 = synth.CSC(A.nrows, A.ncols, A.colptr, A.rowidx, A.val * scale)
+        assert_matches(C, oracle.spgemm(A2, B), EPS["f64"])
+
+
+@pytest.mark.slow
+def test_er_full_size_sampled_rows(pb):
+    """The bench workload (ER n=2^21, d=8) in the bench's launch configuration."""
+    n, d = 1 << 21, 8
+    A, B = synth.er(n, d, seed=1)
+    C = run(pb, A, B)
+    assert_csr_valid(C, n)
+    rows = np.random.default_rng(0).choice(n, 2000, replace=False)
+    rows = np.concatenate([rows, [0, n - 1]])
+    assert_rows_match(C, oracle.spgemm(A, B, rows), EPS["f64"])
+    nnz = int(C.rowptr[-1].item())
+    assert nnz <= n * d * d
