@@ -148,7 +148,10 @@ pb_status pb_plan_query(const pb_plan *plan, int64_t *flop, int64_t *c_cap, size
  * be reused after the stream reaches this call's end.  A and B must have the
  * structure the plan was made from.  C->cap must be >= nnz(C) (c_cap always
  * suffices); otherwise the device records PB_ERR_OVERFLOW and writes nothing
- * past cap.  Errors: INVALID_ARG, SHAPE, WORKSPACE, CUDA.
+ * past cap.  In every case *C->nnz_dev (if set) receives nnz(C).
+ * Counting run: with C->cap == 0 and all four C arrays NULL the call writes
+ * only *C->nnz_dev, so a caller can size C exactly before the real call.
+ * Errors: INVALID_ARG, SHAPE, WORKSPACE, CUDA.
  */
 pb_status pb_spgemm_numeric(pb_handle *h, const pb_plan *plan, const pb_csc *A, const pb_csr *B,
                             pb_csr_out *C, void *workspace, size_t ws_bytes, pb_stream_t stream);

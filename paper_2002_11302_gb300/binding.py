@@ -209,6 +209,9 @@ def set_phase_events(handle: "Handle", events) -> None:
     if events is None:
         _check(handle.lib, handle.ptr, handle.lib.pb_set_phase_events(handle.ptr, None))
         return
+    for e in events:
+        if not e.cuda_event:
+            e.record()  # torch creates the CUDA event lazily, on first record
     arr = (ctypes.c_void_p * 4)(*[int(e.cuda_event) for e in events])
     handle._events = (events, arr)  # keep alive
     _check(handle.lib, handle.ptr, handle.lib.pb_set_phase_events(handle.ptr, arr))

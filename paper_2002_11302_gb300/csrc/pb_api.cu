@@ -44,8 +44,14 @@ struct pb_plan {
     int32_t *bin_row = nullptr, *chunk_k = nullptr;
     PlanHeader *dhdr = nullptr;
     uint32_t *err = nullptr;
+    int64_t *over_scan = nullptr, *over_bin = nullptr, *over_chunk_off = nullptr, *over_tuple_off = nullptr;
+    void *over_map_mem = nullptr;
+    size_t over_map_bytes = 0;
+    int32_t *over_chunk_bin = nullptr;
+    int over_passes = 0;
     // workspace layout of the numeric phase
-    size_t ws_keys = 0, ws_vals = 0, ws_cursor = 0, ws_status = 0, ws_ctrl = 0, ws_bytes = 0;
+    size_t ws_keys = 0, ws_vals = 0, ws_cursor = 0, ws_status = 0, ws_ctrl = 0;
+    size_t ws_skeys = 0, ws_svals = 0, ws_hist = 0, ws_over_u = 0, ws_bytes = 0;
 };
 
 namespace {
@@ -109,6 +115,8 @@ pb_status check_operands(pb_handle *h, const pb_csc *A, const pb_csr *B) {
 void free_plan_memory(pb_plan *p) {
     if (!p || !p->h) return;
     if (p->chunk_mem) p->h->free_fn(p->chunk_mem, p->chunk_bytes, nullptr, p->h->ctx);
+    if (p->over_map_mem) p->h->free_fn(p->over_map_mem, p->over_map_bytes, nullptr, p->h->ctx);
+    p->over_map_mem = nullptr;
     if (p->arena) p->h->free_fn(p->arena, p->arena_bytes, nullptr, p->h->ctx);
     p->chunk_mem = p->arena = nullptr;
 }
@@ -205,6 +213,7 @@ pb_status pb_spgemm_symbolic(pb_handle *h, const pb_csc *A, const pb_csr *B, pb_
     const size_t oF = take(8 * (k + 1)), oR = take(8 * (m + 1)), oFl = take(8 * (m + 1));
     const size_t oRi = take(8 * (m > 0 ? m : 1)), oBr = take(4 * (m + 2)), oBo = take(8 * (m + 2));
     const size_t oH = take(sizeof(PlanHeader)), oT = take(8 * scan_tmp_elems(scan_n)), oE = take(64);
+    const size_t oOs = take(8 * (m + 1)), oOb = take(8 * (m + 1)), oOc = take(8 * (m + 1)), oOt = take(8 * (m + 1));
     p->arena_bytes = off;
     p->arena = h->alloc(p->arena_bytes, stream_, h->ctx);
     if (!p->arena) {
@@ -221,6 +230,10 @@ pb_status pb_spgemm_symbolic(pb_handle *h, const pb_csc *A, const pb_csr *B, pb_
     p->dhdr = reinterpret_cast<PlanHeader *>(base + oH);
     p->scan_tmp = reinterpret_cast<int64_t *>(base + oT);
     p->err = reinterpret_cast<uint32_t *>(base + oE);
+    p->over_scan = reinterpret_cast<int64_t *>(base + oOs);
+    p->over_bin = reinterpret_cast<int64_t *>(base + oOb);
+    p->over_chunk_off = reinterpret_cast<int64_t *>(base + oOc);
+    p->over_tuple_off = reinterpret_cast<int64_t *>(base + oOt);
 
     auto bail = [&](pb_status code) {
         free_plan_memory(p);
@@ -251,6 +264,10 @@ pb_status pb_spgemm_symbolic(pb_handle *h, const pb_csc *A, const pb_csr *B, pb_
     a.rmax_log2 = p->rmax_log2;
     a.capacity = p->capacity;
     a.heavy = p->heavy;
+    a.over_scan = p->over_scan;
+    a.over_bin = p->over_bin;
+    a.over_chunk_off = p->over_chunk_off;
+    a.over_tuple_off = p->over_tuple_off;
     if ((e = launch_symbolic(a, p->scan_tmp, s)) != cudaSuccess) {
         cuda_fail(h, e, "symbolic launch");
         return bail(PB_ERR_CUDA);
@@ -261,12 +278,24 @@ pb_status pb_spgemm_symbolic(pb_handle *h, const pb_csc *A, const pb_csr *B, pb_
         cuda_fail(h, e, "symbolic readback");
         return bail(PB_ERR_CUDA);
     }
-    if (p->hdr.n_oversize > 0) {
-        char msg[200];
-        snprintf(msg, sizeof msg, "%lld bin(s) exceed the on-chip capacity of %d tuples (largest %llu)",
-                 (long long)p->hdr.n_oversize, p->capacity, (unsigned long long)p->hdr.max_bin_count);
-        fail(h, PB_ERR_UNSUPPORTED, msg);
+    if (p->hdr.max_bin_count > 0x7fffffffull) {
+        fail(h, PB_ERR_UNSUPPORTED, "a single row produces 2^31 or more tuples");
         return bail(PB_ERR_UNSUPPORTED);
+    }
+    // Oversize bins: work-item map for their global-memory radix sort.
+    if (p->hdr.n_oversize > 0) {
+        p->over_passes = (p->colbits + 7) / 8;
+        p->over_map_bytes = align256(4 * (size_t)p->hdr.over_chunks);
+        p->over_map_mem = h->alloc(p->over_map_bytes, stream_, h->ctx);
+        if (!p->over_map_mem) {
+            fail(h, PB_ERR_OOM, "oversize map allocation failed");
+            return bail(PB_ERR_OOM);
+        }
+        p->over_chunk_bin = static_cast<int32_t *>(p->over_map_mem);
+        if ((e = launch_over_chunk_map(p->over_chunk_off, p->hdr.n_oversize, p->over_chunk_bin, s)) != cudaSuccess) {
+            cuda_fail(h, e, "oversize map");
+            return bail(PB_ERR_CUDA);
+        }
     }
     // Expand work items.
     p->nchunks = ceil_div<int64_t>(p->hdr.flop, p->chunk);
@@ -297,6 +326,15 @@ pb_status pb_spgemm_symbolic(pb_handle *h, const pb_csc *A, const pb_csr *B, pb_
     w += align256(8 * nb);
     p->ws_ctrl = w;
     w += 256;
+    const size_t OT = (size_t)p->hdr.over_tuples, OC = (size_t)p->hdr.over_chunks, NO = (size_t)p->hdr.n_oversize;
+    p->ws_skeys = w;
+    w += align256(4 * OT);
+    p->ws_svals = w;
+    w += align256(tuple_val_bytes(dtype) * OT);
+    p->ws_hist = w;
+    w += align256(4 * 256 * OC);
+    p->ws_over_u = w;
+    w += align256(8 * NO);
     p->ws_bytes = w;
     *out = p;
     return PB_OK;
@@ -354,7 +392,34 @@ static pb_status fill_numeric(pb_handle *h, const pb_plan *p, const pb_csc *A, c
     a.err = p->err;
     a.dtype = p->dtype;
     a.num_sms = h->num_sms;
+    a.over_scan = p->over_scan;
+    a.over_tuple_off = p->over_tuple_off;
+    a.over_u = reinterpret_cast<int64_t *>(w + p->ws_over_u);
+    a.skeys = reinterpret_cast<uint32_t *>(w + p->ws_skeys);
+    a.svals = w + p->ws_svals;
+    a.over_passes = p->over_passes;
     return PB_OK;
+}
+
+static OversizeArgs oversize_args(const pb_plan *p, void *workspace) {
+    char *w = static_cast<char *>(workspace);
+    OversizeArgs o{};
+    o.R = p->R;
+    o.bin_row = p->bin_row;
+    o.bin_off = p->bin_off;
+    o.over_bin = p->over_bin;
+    o.over_chunk_off = p->over_chunk_off;
+    o.over_tuple_off = p->over_tuple_off;
+    o.over_chunk_bin = p->over_chunk_bin;
+    o.n_over = p->hdr.n_oversize;
+    o.over_chunks = p->hdr.over_chunks;
+    o.keys = reinterpret_cast<uint32_t *>(w + p->ws_keys);
+    o.vals = w + p->ws_vals;
+    o.skeys = reinterpret_cast<uint32_t *>(w + p->ws_skeys);
+    o.svals = w + p->ws_svals;
+    o.hist = reinterpret_cast<uint32_t *>(w + p->ws_hist);
+    o.over_u = reinterpret_cast<int64_t *>(w + p->ws_over_u);
+    return o;
 }
 
 pb_status pb_spgemm_numeric(pb_handle *h, const pb_plan *p, const pb_csc *A, const pb_csr *B, pb_csr_out *C,
@@ -365,10 +430,12 @@ pb_status pb_spgemm_numeric(pb_handle *h, const pb_plan *p, const pb_csc *A, con
     pb_status st = fill_numeric(h, p, A, B, workspace, ws_bytes, a);
     if (st != PB_OK) return st;
     if (C->nrows != p->m || C->ncols != p->n) return fail(h, PB_ERR_SHAPE, "C must be A.nrows x B.ncols");
-    if ((C->rowptr64 == nullptr) == (C->rowptr32 == nullptr))
+    const bool count_only = C->cap == 0 && !C->colidx && !C->val && !C->rowptr64 && !C->rowptr32;
+    if (!count_only && (C->rowptr64 == nullptr) == (C->rowptr32 == nullptr))
         return fail(h, PB_ERR_INVALID_ARG, "exactly one of C.rowptr64 / C.rowptr32 must be set");
     if (C->cap < 0 || (C->cap > 0 && (!C->colidx || !C->val)))
         return fail(h, PB_ERR_INVALID_ARG, "C arrays must not be NULL when cap > 0");
+    a.count_only = count_only ? 1 : 0;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream_);
     a.rowptr64 = C->rowptr64;
     a.rowptr32 = C->rowptr32;
@@ -392,6 +459,8 @@ pb_status pb_spgemm_numeric(pb_handle *h, const pb_plan *p, const pb_csc *A, con
     PB_CUDA(h, cudaMemsetAsync(w + p->ws_ctrl, 0, 256, s));
     if (h->phase_on) PB_CUDA(h, cudaEventRecord(h->phase_ev[1], s));
     PB_CUDA(h, launch_expand(a, s));
+    if (p->hdr.n_oversize > 0)
+        PB_CUDA(h, launch_oversize(oversize_args(p, workspace), p->over_passes, p->dtype, h->num_sms, s));
     if (h->phase_on) PB_CUDA(h, cudaEventRecord(h->phase_ev[2], s));
     PB_CUDA(h, launch_binsort(a, s));
     if (h->phase_on) PB_CUDA(h, cudaEventRecord(h->phase_ev[3], s));

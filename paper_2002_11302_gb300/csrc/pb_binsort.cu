@@ -47,7 +47,6 @@ struct SortSmem {
     int32_t ok;
 };
 
-template <class OV>
 __device__ inline void write_rowptr(const NumericArgs &p, int64_t row, int64_t v) {
     if (p.rowptr64)
         p.rowptr64[row] = v;
@@ -104,6 +103,61 @@ __device__ inline int64_t lookback(uint64_t *status, int64_t b, uint64_t agg, ui
     return (int64_t)prefix;
 }
 
+// Thread 0: publish this bin's merged count, find its prefix, check C's
+// capacity, and let the last bin write nnz(C) and the final row pointer.
+__device__ inline void publish_and_check(const NumericArgs &p, int64_t b, int64_t U, int64_t *prefix, int32_t *ok) {
+    const int64_t P = lookback(p.status, b, (uint64_t)U, p.err);
+    *prefix = P;
+    int32_t good = p.count_only ? 0 : 1;
+    if (!p.count_only && (P + U > p.cap || (p.rowptr32 && P + U > 0x7fffffffll))) {
+        atomicOr(p.err, DEV_ERR_OVERFLOW);
+        good = 0;
+    }
+    *ok = good;
+    if (b == p.nbins - 1) {
+        if (good) write_rowptr(p, p.m, P + U);
+        if (p.nnz_dev) *p.nnz_dev = P + U;
+    }
+}
+
+// An oversize bin (one row, more tuples than the on-chip capacity) was sorted
+// in global memory before this kernel and its merged count is known: publish
+// it at once, then stream the sorted run and write the merged entries.
+template <int THREADS, class TV, class OV>
+__device__ void stream_oversize_bin(const NumericArgs &p, int64_t b, int32_t row0, int32_t row1, int64_t off,
+                                    int64_t N, uint32_t colmask, int64_t *scratch, int64_t *prefix, int32_t *okp) {
+    const int tid = threadIdx.x;
+    const int64_t o = p.over_scan[b];
+    const bool in_scratch = (p.over_passes & 1) != 0;
+    const uint32_t *k = in_scratch ? p.skeys + p.over_tuple_off[o] : p.keys + off;
+    const TV *v = in_scratch ? static_cast<const TV *>(p.svals) + p.over_tuple_off[o]
+                             : static_cast<const TV *>(p.vals) + off;
+    OV *valC = static_cast<OV *>(p.valC);
+    if (tid == 0) publish_and_check(p, b, p.over_u[o], prefix, okp);
+    __syncthreads();
+    const int64_t P = *prefix;
+    const bool ok = *okp != 0;
+    if (ok)
+        for (int32_t r = row0 + tid; r < row1; r += THREADS) write_rowptr(p, r, r == row0 ? P : P + p.over_u[o]);
+    int64_t running = 0;
+    for (int64_t base = 0; base < N; base += THREADS) {
+        const int64_t q = base + tid;
+        const bool valid = q < N;
+        const uint32_t key = valid ? k[q] : 0u;
+        const bool head = valid && (q == 0 || k[q - 1] != key);
+        int64_t chunk_total;
+        const int64_t u = block_exclusive_scan<int64_t, THREADS>(head ? 1 : 0, scratch, &chunk_total);
+        if (head && ok) {
+            double acc = (double)v[q];
+            for (int64_t r = q + 1; r < N && k[r] == key; ++r) acc += (double)v[r];
+            p.colidx[P + running + u] = (int32_t)(key & colmask);
+            valC[P + running + u] = (OV)acc;
+        }
+        running += chunk_total;
+    }
+    __syncthreads();
+}
+
 template <int CAP, int THREADS, class TV, class OV>
 __global__ void __launch_bounds__(THREADS, (CAP <= 4096 ? 2 : 1)) k_binsort(const NumericArgs p) {
     using S = SortSmem<CAP, THREADS, TV>;
@@ -130,12 +184,14 @@ __global__ void __launch_bounds__(THREADS, (CAP <= 4096 ? 2 : 1)) k_binsort(cons
         if (b >= p.nbins) break;
         const int32_t row0 = p.bin_row[b], row1 = p.bin_row[b + 1];
         const int64_t off = p.bin_off[b];
-        int N = (int)(p.R[row1] - p.R[row0]);
-        bool loaded = true;
-        if (N > CAP) {
-            if (tid == 0) atomicOr(p.err, DEV_ERR_CAPACITY);
-            N = 0;
+        const int64_t Nfull = p.R[row1] - p.R[row0];
+        if (Nfull > CAP) {
+            stream_oversize_bin<THREADS, TV, OV>(p, b, row0, row1, off, Nfull, colmask, sm.scratch, &sm.prefix,
+                                                 &sm.ok);
+            continue;
         }
+        int N = (int)Nfull;
+        bool loaded = true;
         // ---- load the bin (bulk copies, 16-byte granules) -------------------
         if (N > 0) {
             const uint32_t n4 = (uint32_t)((N + 3) & ~3);
@@ -316,27 +372,14 @@ __global__ void __launch_bounds__(THREADS, (CAP <= 4096 ? 2 : 1)) k_binsort(cons
             }
         }
         const int64_t U = block_reduce_sum<int64_t, THREADS>(local_u, sm.scratch);
-        if (tid == 0) {
-            const int64_t P = lookback(p.status, b, (uint64_t)U, p.err);
-            sm.prefix = P;
-            sm.ok = 1;
-            if (P + U > p.cap || (p.rowptr32 && P + U > 0x7fffffffll)) {
-                atomicOr(p.err, DEV_ERR_OVERFLOW);
-                sm.ok = 0;
-            }
-        }
+        if (tid == 0) publish_and_check(p, b, U, &sm.prefix, &sm.ok);
         __syncthreads();
         const int64_t P = sm.prefix;
         const bool ok = sm.ok != 0;
         // ---- row pointers of this bin's rows -----------------------------------
         smem_exclusive_scan<THREADS>(sm.cnt, rows_b, sm.scratch);
-        if (ok) {
-            for (int r = tid; r < rows_b; r += THREADS) write_rowptr<OV>(p, row0 + r, P + sm.cnt[r]);
-            if (b == p.nbins - 1 && tid == 0) {
-                write_rowptr<OV>(p, p.m, P + U);
-                if (p.nnz_dev) *p.nnz_dev = P + U;
-            }
-        }
+        if (ok)
+            for (int r = tid; r < rows_b; r += THREADS) write_rowptr(p, row0 + r, P + sm.cnt[r]);
         // ---- merged entries in key order ---------------------------------------
         int64_t running = 0;
         for (int base = 0; base < N; base += THREADS) {

@@ -27,6 +27,9 @@ constexpr uint64_t LB_VALUE_MASK = (1ull << LB_FLAG_SHIFT) - 1;
 // Bounded spin: every device wait gives up after this many polls.
 constexpr uint32_t SPIN_LIMIT = 1u << 24;
 
+// Tuples per work item of the oversize-bin sort.
+constexpr int OVER_CHUNK = 4096;
+
 // Plan header filled on the device by the symbolic phase, read back once.
 struct PlanHeader {
     int64_t flop;
@@ -35,7 +38,8 @@ struct PlanHeader {
     unsigned long long max_bin_count;
     unsigned long long max_light_row;  // largest per-row flop among rows <= heavy threshold
     int64_t n_oversize;      // bins holding more than bin_capacity tuples
-    int64_t pad[2];
+    int64_t over_chunks;     // OVER_CHUNK-tuple work items over all oversize bins
+    int64_t over_tuples;     // sum over oversize bins of round_up(count, 4)
 };
 
 // Arguments of the kernels (passed by value).
@@ -51,6 +55,26 @@ struct SymbolicArgs {
     PlanHeader *hdr;
     int32_t colbits, rmax_log2;
     int64_t capacity, heavy;
+    // oversize-bin lists (upper bound m+1 entries each)
+    int64_t *over_scan;       // exclusive index of each bin among oversize bins
+    int64_t *over_bin;        // bin id of oversize bin o
+    int64_t *over_chunk_off;  // first work item of oversize bin o
+    int64_t *over_tuple_off;  // scratch offset of oversize bin o
+};
+
+struct OversizeArgs {
+    const int64_t *R;
+    const int32_t *bin_row;
+    const int64_t *bin_off;
+    const int64_t *over_bin, *over_chunk_off, *over_tuple_off;
+    const int32_t *over_chunk_bin;  // [over_chunks] oversize bin of each work item
+    int64_t n_over, over_chunks;
+    uint32_t *keys;
+    void *vals;
+    uint32_t *skeys;
+    void *svals;
+    uint32_t *hist;   // [over_chunks * 256]
+    int64_t *over_u;  // [n_over] merged entries of each oversize bin
 };
 
 template <class T>
@@ -181,6 +205,9 @@ void count_launches(int64_t n);
 cudaError_t launch_symbolic(const SymbolicArgs &a, int64_t *scan_tmp, cudaStream_t s);
 cudaError_t launch_chunk_table(const int64_t *F, int32_t k, int64_t flop, int64_t chunk, int32_t *chunk_k,
                                cudaStream_t s);
+cudaError_t launch_over_chunk_map(const int64_t *over_chunk_off, int64_t n_over, int32_t *over_chunk_bin,
+                                  cudaStream_t s);
+cudaError_t launch_oversize(const OversizeArgs &a, int passes, int dtype, int num_sms, cudaStream_t s);
 
 struct NumericArgs {
     // inputs
@@ -210,8 +237,15 @@ struct NumericArgs {
     void *valC;
     int64_t *nnz_dev;
     int64_t cap;
+    int count_only;      // compute nnz(C) only: no writes to C except *nnz_dev
     int dtype;
     int num_sms;
+    // oversize bins (sorted in global memory before the sort kernel)
+    const int64_t *over_scan, *over_tuple_off;
+    const int64_t *over_u;
+    uint32_t *skeys;
+    void *svals;
+    int over_passes;
 };
 
 cudaError_t launch_expand(const NumericArgs &a, cudaStream_t s);

@@ -97,28 +97,60 @@ __global__ void k_bin_sizes(const int64_t *R, const int32_t *bin_row, int64_t ca
                             int64_t *bin_off) {
     const int64_t nbins = hdr->nbins;
     unsigned long long mx = 0;
-    long long over = 0;
     for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < nbins; b += (int64_t)gridDim.x * blockDim.x) {
         const int64_t cnt = R[bin_row[b + 1]] - R[bin_row[b]];
         bin_off[b] = (cnt + 3) & ~int64_t(3);
         if ((unsigned long long)cnt > mx) mx = cnt;
-        if (cnt > capacity) ++over;
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         unsigned long long t = __shfl_down_sync(FULL, mx, o);
         mx = t > mx ? t : mx;
-        over += __shfl_down_sync(FULL, over, o);
     }
     if ((threadIdx.x & 31) == 0) {
         if (mx) atomicMax(&hdr->max_bin_count, mx);
-        if (over) atomicAdd(reinterpret_cast<unsigned long long *>(&hdr->n_oversize), (unsigned long long)over);
     }
 }
 
-__global__ void k_finish_header(const int64_t *F, int32_t k, const int64_t *bin_off, PlanHeader *hdr) {
+__device__ inline int64_t bin_count(const int64_t *R, const int32_t *bin_row, int64_t b) {
+    return R[bin_row[b + 1]] - R[bin_row[b]];
+}
+
+__global__ void k_over_flags(const int64_t *R, const int32_t *bin_row, int64_t capacity, const PlanHeader *hdr,
+                             int64_t *over_scan) {
+    const int64_t nbins = hdr->nbins;
+    for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < nbins; b += (int64_t)gridDim.x * blockDim.x)
+        over_scan[b] = bin_count(R, bin_row, b) > capacity ? 1 : 0;
+}
+
+// over_scan is now the exclusive scan of the oversize flags.
+__global__ void k_over_list(const int64_t *R, const int32_t *bin_row, int64_t capacity, const PlanHeader *hdr,
+                            const int64_t *over_scan, int64_t *over_bin, int64_t *over_chunk_off,
+                            int64_t *over_tuple_off) {
+    const int64_t nbins = hdr->nbins;
+    for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < nbins; b += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t n = bin_count(R, bin_row, b);
+        if (n <= capacity) continue;
+        const int64_t o = over_scan[b];
+        over_bin[o] = b;
+        over_chunk_off[o] = (n + OVER_CHUNK - 1) / OVER_CHUNK;
+        over_tuple_off[o] = (n + 3) & ~int64_t(3);
+    }
+}
+
+__global__ void k_finish_header(const int64_t *F, int32_t k, int32_t m, const int64_t *bin_off,
+                                const int64_t *over_scan, const int64_t *over_chunk_off,
+                                const int64_t *over_tuple_off, PlanHeader *hdr) {
     hdr->flop = F[k];
     hdr->tuples_padded = bin_off[hdr->nbins];
+    hdr->n_oversize = over_scan[m];
+    hdr->over_chunks = over_chunk_off[m];
+    hdr->over_tuples = over_tuple_off[m];
+}
+
+__global__ void k_over_chunk_map(const int64_t *over_chunk_off, int64_t n_over, int32_t *over_chunk_bin) {
+    for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < n_over; o += (int64_t)gridDim.x * blockDim.x)
+        for (int64_t c = over_chunk_off[o]; c < over_chunk_off[o + 1]; ++c) over_chunk_bin[c] = (int32_t)o;
 }
 
 // Chunk table for the expand phase: chunk c starts at tuple c*chunk, which
@@ -161,8 +193,28 @@ cudaError_t launch_symbolic(const SymbolicArgs &a, int64_t *scan_tmp, cudaStream
     if ((e = cudaMemsetAsync(a.bin_off, 0, sizeof(int64_t) * ((size_t)a.m + 2), s)) != cudaSuccess) return e;
     k_bin_sizes<<<grid_for(a.m, T), T, 0, s>>>(a.R, a.bin_row, a.capacity, a.hdr, a.bin_off);
     if ((e = scan_i64(a.bin_off, a.m, scan_tmp, s)) != cudaSuccess) return e;
-    k_finish_header<<<1, 1, 0, s>>>(a.F, a.k, a.bin_off, a.hdr);
-    count_launches(8);  // the non-scan kernels above
+    // 5. oversize bins (single rows above the on-chip capacity): list, work items, scratch offsets
+    const size_t mb = sizeof(int64_t) * ((size_t)a.m + 1);
+    if ((e = cudaMemsetAsync(a.over_scan, 0, mb, s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(a.over_chunk_off, 0, mb, s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(a.over_tuple_off, 0, mb, s)) != cudaSuccess) return e;
+    k_over_flags<<<grid_for(a.m, T), T, 0, s>>>(a.R, a.bin_row, a.capacity, a.hdr, a.over_scan);
+    if ((e = scan_i64(a.over_scan, a.m, scan_tmp, s)) != cudaSuccess) return e;
+    k_over_list<<<grid_for(a.m, T), T, 0, s>>>(a.R, a.bin_row, a.capacity, a.hdr, a.over_scan, a.over_bin,
+                                                a.over_chunk_off, a.over_tuple_off);
+    if ((e = scan_i64(a.over_chunk_off, a.m, scan_tmp, s)) != cudaSuccess) return e;
+    if ((e = scan_i64(a.over_tuple_off, a.m, scan_tmp, s)) != cudaSuccess) return e;
+    k_finish_header<<<1, 1, 0, s>>>(a.F, a.k, a.m, a.bin_off, a.over_scan, a.over_chunk_off, a.over_tuple_off,
+                                    a.hdr);
+    count_launches(10);  // the non-scan kernels above
+    return cudaGetLastError();
+}
+
+cudaError_t launch_over_chunk_map(const int64_t *over_chunk_off, int64_t n_over, int32_t *over_chunk_bin,
+                                  cudaStream_t s) {
+    if (n_over <= 0) return cudaSuccess;
+    k_over_chunk_map<<<grid_for(n_over, 256), 256, 0, s>>>(over_chunk_off, n_over, over_chunk_bin);
+    count_launches(1);
     return cudaGetLastError();
 }
 
