@@ -40,6 +40,8 @@ WORKLOADS = {
                  desc="ER C=A*A, n=2^21, d=8 per column, FP64 values U(-1,1), int32 indices"),
     "er22": dict(kind="er", n=1 << 22, d=8, seed=4, dtype="f64",
                  desc="ER C=A*A, n=2^22, d=8 per column, FP64 values U(-1,1), int32 indices"),
+    "er19": dict(kind="er", n=1 << 19, d=8, seed=7, dtype="f64",
+                 desc="ER C=A*A, n=2^19, d=8 per column, FP64 values U(-1,1), int32 indices"),
     "er12": dict(kind="er", n=4096, d=4, seed=0, dtype="f64",
                  desc="ER C=A*A, n=4096, d=4 per column, FP64 values U(-1,1), int32 indices"),
 }
@@ -196,7 +198,8 @@ def run_ours(args, w):
     Ad, Bd = binding.csc_to_device(A), binding.csr_to_device(B)
     handle = binding.Handle()
     stream = torch.cuda.current_stream()
-    plan = binding.symbolic(Ad, Bd, handle=handle)
+    cfg = binding.make_config(bin_capacity=args.capacity, expand_chunk=args.chunk)
+    plan = binding.symbolic(Ad, Bd, config=cfg, handle=handle)
     flop = plan.flop
     C = binding.alloc_output(plan, rowptr64=True)
     ws = plan.workspace()
@@ -206,7 +209,7 @@ def run_ours(args, w):
     def step(record=None):
         if record is not None:
             record[0].record(stream)
-        p = binding.symbolic(Ad, Bd, handle=handle)
+        p = binding.symbolic(Ad, Bd, config=cfg, handle=handle)
         if record is not None:
             record[1].record(stream)
         binding.numeric(p, Ad, Bd, C, ws)
@@ -275,7 +278,7 @@ def run_ours(args, w):
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": w["desc"], "n": w["n"], "d": w["d"], "flop": flop, "nnz_c": nnz_c,
-                   "cf": flop / max(nnz_c, 1), "nbins": plan.nbins,
+                   "cf": flop / max(nnz_c, 1), "nbins": plan.nbins, "bin_capacity": args.capacity or 4096,
                    "l2": "no flush: inputs (0.4 GB) and tuples (1.6 GB) exceed the 129 MB L2",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": hbm, "unit": "GB/s",
@@ -356,6 +359,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="er21")
+    ap.add_argument("--capacity", type=int, default=0, help="tuples per on-chip bin (2048/4096/8192; 0 = default)")
+    ap.add_argument("--chunk", type=int, default=0, help="tuples per expand work item (0 = default)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

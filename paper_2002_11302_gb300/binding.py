@@ -12,6 +12,7 @@ Names follow the C ABI: ``symbolic`` / ``numeric`` / ``plan_status`` mirror
 from __future__ import annotations
 
 import ctypes
+import os
 import threading
 from dataclasses import dataclass
 from typing import Optional
@@ -92,7 +93,7 @@ def load_library(path: Optional[str] = None):
     global _lib
     with _lib_lock:
         if _lib is None:
-            lib = ctypes.CDLL(path or _build.build())
+            lib = ctypes.CDLL(path or os.environ.get("PB_LIBRARY") or _build.build())
             for name, (res, args) in SIGNATURES.items():
                 fn = getattr(lib, name)
                 fn.restype = res

@@ -32,7 +32,7 @@ struct pb_plan {
     int64_t nnzA = 0, nnzB = 0;
     pb_dtype dtype = PB_F64;
     int32_t colbits = 1, rmax_log2 = 0, capacity = 4096;
-    int64_t heavy = 0, chunk = 1024, nchunks = 0;
+    int64_t heavy = 0, chunk = 4096, nchunks = 0;
     PlanHeader hdr{};
     // device arrays (one arena + the chunk table)
     void *arena = nullptr;
@@ -40,8 +40,8 @@ struct pb_plan {
     void *chunk_mem = nullptr;
     size_t chunk_bytes = 0;
     int64_t *F = nullptr, *R = nullptr, *flags = nullptr, *bin_off = nullptr, *scan_tmp = nullptr;
-    uint64_t *rowinfo = nullptr;
-    int32_t *bin_row = nullptr, *chunk_k = nullptr;
+    uint64_t *rowinfo = nullptr, *ainfo = nullptr;
+    int32_t *bin_row = nullptr, *chunk_e = nullptr, *acol = nullptr;
     PlanHeader *dhdr = nullptr;
     uint32_t *err = nullptr;
     int64_t *over_scan = nullptr, *over_bin = nullptr, *over_chunk_off = nullptr, *over_tuple_off = nullptr;
@@ -186,7 +186,7 @@ pb_status pb_spgemm_symbolic(pb_handle *h, const pb_csc *A, const pb_csr *B, pb_
         return fail(h, PB_ERR_UNSUPPORTED, "B.ncols too large for a 32-bit key");
     }
     int rowbits = 32 - p->colbits;
-    p->rmax_log2 = rowbits < 12 ? rowbits : 12;
+    p->rmax_log2 = rowbits < RMAX_LOG2 ? rowbits : RMAX_LOG2;
     if (cfg && cfg->bin_capacity) p->capacity = cfg->bin_capacity;
     if (p->capacity != 2048 && p->capacity != 4096 && p->capacity != 8192) {
         delete p;
@@ -214,6 +214,7 @@ pb_status pb_spgemm_symbolic(pb_handle *h, const pb_csc *A, const pb_csr *B, pb_
     const size_t oRi = take(8 * (m > 0 ? m : 1)), oBr = take(4 * (m + 2)), oBo = take(8 * (m + 2));
     const size_t oH = take(sizeof(PlanHeader)), oT = take(8 * scan_tmp_elems(scan_n)), oE = take(64);
     const size_t oOs = take(8 * (m + 1)), oOb = take(8 * (m + 1)), oOc = take(8 * (m + 1)), oOt = take(8 * (m + 1));
+    const size_t oAi = take(8 * (p->nnzA > 0 ? p->nnzA : 1)), oAc = take(4 * (p->nnzA > 0 ? p->nnzA : 1));
     p->arena_bytes = off;
     p->arena = h->alloc(p->arena_bytes, stream_, h->ctx);
     if (!p->arena) {
@@ -234,6 +235,8 @@ pb_status pb_spgemm_symbolic(pb_handle *h, const pb_csc *A, const pb_csr *B, pb_
     p->over_bin = reinterpret_cast<int64_t *>(base + oOb);
     p->over_chunk_off = reinterpret_cast<int64_t *>(base + oOc);
     p->over_tuple_off = reinterpret_cast<int64_t *>(base + oOt);
+    p->ainfo = reinterpret_cast<uint64_t *>(base + oAi);
+    p->acol = reinterpret_cast<int32_t *>(base + oAc);
 
     auto bail = [&](pb_status code) {
         free_plan_memory(p);
@@ -257,6 +260,8 @@ pb_status pb_spgemm_symbolic(pb_handle *h, const pb_csc *A, const pb_csr *B, pb_
     a.R = p->R;
     a.flags = p->flags;
     a.rowinfo = p->rowinfo;
+    a.ainfo = p->ainfo;
+    a.nnzA = p->nnzA;
     a.bin_row = p->bin_row;
     a.bin_off = p->bin_off;
     a.hdr = p->dhdr;
@@ -297,20 +302,19 @@ pb_status pb_spgemm_symbolic(pb_handle *h, const pb_csc *A, const pb_csr *B, pb_
             return bail(PB_ERR_CUDA);
         }
     }
-    // Expand work items.
+    // Expand work items (A-entry granularity) and the column of every A entry.
     p->nchunks = ceil_div<int64_t>(p->hdr.flop, p->chunk);
-    if (p->nchunks > 0) {
-        p->chunk_bytes = align256(4 * (size_t)p->nchunks);
-        p->chunk_mem = h->alloc(p->chunk_bytes, stream_, h->ctx);
-        if (!p->chunk_mem) {
-            fail(h, PB_ERR_OOM, "chunk table allocation failed");
-            return bail(PB_ERR_OOM);
-        }
-        p->chunk_k = static_cast<int32_t *>(p->chunk_mem);
-        if ((e = launch_chunk_table(p->F, p->k, p->hdr.flop, p->chunk, p->chunk_k, s)) != cudaSuccess) {
-            cuda_fail(h, e, "chunk table");
-            return bail(PB_ERR_CUDA);
-        }
+    p->chunk_bytes = align256(4 * ((size_t)p->nchunks + 1));
+    p->chunk_mem = h->alloc(p->chunk_bytes, stream_, h->ctx);
+    if (!p->chunk_mem) {
+        fail(h, PB_ERR_OOM, "chunk table allocation failed");
+        return bail(PB_ERR_OOM);
+    }
+    p->chunk_e = static_cast<int32_t *>(p->chunk_mem);
+    if ((e = launch_chunk_table(p->F, A->colptr, B->rowptr, p->k, p->nnzA, p->nchunks, p->chunk, p->chunk_e, p->acol,
+                                s)) != cudaSuccess) {
+        cuda_fail(h, e, "chunk table");
+        return bail(PB_ERR_CUDA);
     }
     // Workspace layout of the numeric phase.
     const size_t T = (size_t)p->hdr.tuples_padded;
@@ -321,7 +325,7 @@ pb_status pb_spgemm_symbolic(pb_handle *h, const pb_csc *A, const pb_csr *B, pb_
     p->ws_vals = w;
     w += align256(tuple_val_bytes(dtype) * T);
     p->ws_cursor = w;
-    w += align256(4 * nb);
+    w += align256(8 * nb);
     p->ws_status = w;
     w += align256(8 * nb);
     p->ws_ctrl = w;
@@ -374,10 +378,11 @@ static pb_status fill_numeric(pb_handle *h, const pb_plan *p, const pb_csc *A, c
     a.valB = B->val;
     a.F = p->F;
     a.R = p->R;
-    a.rowinfo = p->rowinfo;
+    a.ainfo = p->ainfo;
     a.bin_row = p->bin_row;
     a.bin_off = p->bin_off;
-    a.chunk_k = p->chunk_k;
+    a.chunk_e = p->chunk_e;
+    a.acol = p->acol;
     a.flop = p->hdr.flop;
     a.nbins = p->hdr.nbins;
     a.nchunks = p->nchunks;
@@ -385,8 +390,8 @@ static pb_status fill_numeric(pb_handle *h, const pb_plan *p, const pb_csc *A, c
     a.colbits = p->colbits;
     a.capacity = p->capacity;
     a.keys = reinterpret_cast<uint32_t *>(w + p->ws_keys);
+    a.cursor = reinterpret_cast<uint64_t *>(w + p->ws_cursor);
     a.vals = w + p->ws_vals;
-    a.cursor = reinterpret_cast<uint32_t *>(w + p->ws_cursor);
     a.status = reinterpret_cast<uint64_t *>(w + p->ws_status);
     a.ticket = reinterpret_cast<uint32_t *>(w + p->ws_ctrl);
     a.err = p->err;
@@ -454,7 +459,7 @@ pb_status pb_spgemm_numeric(pb_handle *h, const pb_plan *p, const pb_csc *A, con
         if (C->nnz_dev) PB_CUDA(h, cudaMemsetAsync(C->nnz_dev, 0, 8, s));
         return PB_OK;
     }
-    PB_CUDA(h, cudaMemsetAsync(w + p->ws_cursor, 0, 4 * nb, s));
+    PB_CUDA(h, cudaMemcpyAsync(w + p->ws_cursor, p->bin_off, 8 * nb, cudaMemcpyDeviceToDevice, s));
     PB_CUDA(h, cudaMemsetAsync(w + p->ws_status, 0, 8 * nb, s));
     PB_CUDA(h, cudaMemsetAsync(w + p->ws_ctrl, 0, 256, s));
     if (h->phase_on) PB_CUDA(h, cudaEventRecord(h->phase_ev[1], s));
@@ -490,7 +495,7 @@ pb_status pb_debug_expand(pb_handle *h, const pb_plan *p, const pb_csc *A, const
     if (st != PB_OK) return st;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream_);
     char *w = static_cast<char *>(workspace);
-    PB_CUDA(h, cudaMemsetAsync(w + p->ws_cursor, 0, 4 * (size_t)p->hdr.nbins, s));
+    PB_CUDA(h, cudaMemcpyAsync(w + p->ws_cursor, p->bin_off, 8 * (size_t)p->hdr.nbins, cudaMemcpyDeviceToDevice, s));
     PB_CUDA(h, launch_expand(a, s));
     return PB_OK;
 }

@@ -4,46 +4,50 @@
 //   load     the bin's keys and values with two bulk global->shared copies
 //            (the bin is read from DRAM exactly once: "in-cache sorting",
 //            Sec. III-D, with shared memory playing the cache);
-//   sort     by the packed (in-bin row, column) key (Sec. III-D).  First a
-//            bucket pass on the top bits of (key - min key) with shared-memory
-//            atomic counters; when every bucket is small (<= 32 tuples, the
-//            common case for ER-like inputs) each bucket is finished by an
-//            insertion sort.  Otherwise a stable LSD radix sort over 8-bit
-//            digits (warp-level multisplit ranking with ballots) sorts the
-//            whole bin.  Both give the same key order; equal keys are merged
-//            next, so their order does not matter;
+//   sort     by the packed (in-bin row, column) key (Sec. III-D).  A bucket
+//            pass on the top bits of (key - min key) with shared-memory atomic
+//            counters places every tuple in its bucket.  When no bucket holds
+//            more than SMALL_BUCKET tuples (the common case for ER-like
+//            inputs), each thread owns a contiguous run of buckets and
+//            finishes them by insertion sort.  Otherwise a stable LSD radix
+//            sort over 8-bit digits (warp-level multisplit ranking with
+//            ballots) sorts the whole bin.  Both give ascending keys; equal
+//            keys are merged next, so their relative order does not matter;
 //   compress equal adjacent keys are summed (Sec. III-E: one pass over the
 //            sorted tuples; sums accumulate in double);
 //   ConvertCSR the bins are concatenated in row order: the bin's number of
 //            merged entries is published and the exclusive prefix over all
-//            earlier bins is found by decoupled look-back (bins are taken in
-//            increasing order through a ticket counter, so every bin a CTA
-//            waits for is already owned by a running CTA); then the column
-//            indices, values and row pointers of the bin's rows are written.
+//            earlier bins is found by a warp-parallel decoupled look-back
+//            (bins are taken in increasing order through a ticket counter, so
+//            every bin a CTA waits for is owned by a running CTA); then the
+//            column indices, values and row pointers of the bin are written.
 #include "pb_common.cuh"
 
 namespace pb {
 
 namespace {
 
-constexpr int RMAX = 4096;     // max rows of one bin (symbolic cuts bins at multiples of this)
+constexpr int RMAX = 1 << RMAX_LOG2;  // max rows of one bin (symbolic cuts bins at multiples of this)
 constexpr int SMALL_BUCKET = 32;
 
 template <int CAP, int THREADS, class TV>
 struct SortSmem {
     static constexpr int NW = THREADS / 32;
-    static constexpr int CNTN = (CAP > 256 * NW ? (CAP > RMAX ? CAP : RMAX) : (256 * NW > RMAX ? 256 * NW : RMAX));
+    static constexpr int CNTN = (CAP + 4 > 256 * NW) ? CAP + 4 : 256 * NW;
     uint32_t kin[CAP];
     TV vin[CAP];
     uint32_t skey[CAP];
     uint16_t sidx[CAP];
     uint16_t sidx2[CAP];
-    uint32_t cnt[CNTN];
+    uint32_t cnt[CNTN];     // bucket counters / offsets, LSD digit counters
+    uint32_t rowcnt[RMAX];  // merged entries per in-bin row
     int64_t scratch[40];
+    uint32_t wtot[NW];      // merged entries per warp segment
+    int32_t marks[2];       // look-back: nearest inclusive prefix / unpublished bin
     uint64_t bar;
     int64_t bin;
     int64_t prefix;
-    uint32_t kmin, kmax, maxb;
+    uint32_t big;
     int32_t ok;
 };
 
@@ -54,7 +58,7 @@ __device__ inline void write_rowptr(const NumericArgs &p, int64_t row, int64_t v
         p.rowptr32[row] = (int32_t)v;
 }
 
-// Exclusive scan in place of cnt[0..n) (n <= CNTN), all threads.
+// Exclusive scan in place of cnt[0..n), blocked per thread; all threads.
 template <int THREADS>
 __device__ inline void smem_exclusive_scan(uint32_t *cnt, int n, int64_t *scratch) {
     const int per = (n + THREADS - 1) / THREADS;
@@ -73,40 +77,146 @@ __device__ inline void smem_exclusive_scan(uint32_t *cnt, int n, int64_t *scratc
     __syncthreads();
 }
 
-// Decoupled look-back over bins (thread 0 only).  Returns the exclusive prefix.
-__device__ inline int64_t lookback(uint64_t *status, int64_t b, uint64_t agg, uint32_t *err) {
+// Exclusive scan in place of cnt[0..n) with n = NW * 32 * V: warp w owns the
+// contiguous segment [w*32V, (w+1)*32V), loads it lane-striped (conflict-free,
+// all V loads in flight), scans the V rows with interleaved warp scans, then
+// the warp totals are combined.
+template <int THREADS, int V>
+__device__ inline void smem_exclusive_scan_striped(uint32_t *cnt, int64_t *scratch) {
+    constexpr int NW = THREADS / 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t *seg = cnt + warp * 32 * V;
+    uint32_t v[V], inc[V];
+#pragma unroll
+    for (int j = 0; j < V; ++j) v[j] = seg[j * 32 + lane];
+#pragma unroll
+    for (int j = 0; j < V; ++j) inc[j] = v[j];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+#pragma unroll
+        for (int j = 0; j < V; ++j) {
+            const uint32_t t = __shfl_up_sync(FULL, inc[j], o);
+            if (lane >= o) inc[j] += t;
+        }
+    }
+    uint32_t run = 0;
+#pragma unroll
+    for (int j = 0; j < V; ++j) {
+        const uint32_t tot = __shfl_sync(FULL, inc[j], 31);
+        v[j] = run + inc[j] - v[j];
+        run += tot;
+    }
+    uint32_t *wsum = reinterpret_cast<uint32_t *>(scratch);
+    if (lane == 0) wsum[warp] = run;
+    __syncthreads();
+    uint32_t base = 0;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) base += (w < warp) ? wsum[w] : 0u;
+#pragma unroll
+    for (int j = 0; j < V; ++j) seg[j * 32 + lane] = v[j] + base;
+    __syncthreads();
+}
+
+__device__ inline uint64_t warp_sum_u64(uint64_t v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+    return v;
+}
+
+// Decoupled look-back, executed by one full warp.  Lane i inspects bin j - i,
+// so each poll covers 32 predecessors.  Returns the exclusive prefix.
+__device__ inline int64_t lookback_warp(uint64_t *status, int64_t b, uint64_t agg, uint32_t *err) {
+    const int lane = threadIdx.x & 31;
     if (b == 0) {
-        st_release_u64(&status[0], LB_PREFIX | agg);
+        if (lane == 0) st_release_u64(&status[0], LB_PREFIX | agg);
         return 0;
     }
-    st_release_u64(&status[b], LB_AGGREGATE | agg);
+    if (lane == 0) st_release_u64(&status[b], LB_AGGREGATE | agg);
     uint64_t prefix = 0;
     int64_t j = b - 1;
+    bool timed_out = false;
     while (true) {
-        uint64_t v;
-        uint32_t spins = 0;
-        while (true) {
-            v = ld_acquire_u64(&status[j]);
-            if (v >> LB_FLAG_SHIFT) break;
-            if (++spins > SPIN_LIMIT) {
-                atomicOr(err, DEV_ERR_TIMEOUT);
-                v = LB_PREFIX;  // give up: treat as prefix 0 so the chain keeps moving
-                break;
+        const int64_t idx = j - lane;
+        uint64_t v = LB_PREFIX;  // before bin 0 the prefix is 0
+        if (idx >= 0) {
+            uint32_t spins = 0;
+            while (true) {
+                v = ld_acquire_u64(&status[idx]);
+                if (v >> LB_FLAG_SHIFT) break;
+                if (++spins > SPIN_LIMIT) {
+                    timed_out = true;
+                    v = LB_PREFIX;  // give up: treat as prefix 0 so the chain keeps moving
+                    break;
+                }
+                __nanosleep(32);
             }
-            __nanosleep(32);
         }
-        prefix += v & LB_VALUE_MASK;
-        if ((v & ~LB_VALUE_MASK) == LB_PREFIX) break;
-        --j;
+        const uint32_t pmask = __ballot_sync(FULL, (v & ~LB_VALUE_MASK) == LB_PREFIX);
+        if (pmask) {
+            const int first = __ffs(pmask) - 1;  // closest predecessor holding an inclusive prefix
+            prefix += warp_sum_u64(lane <= first ? (v & LB_VALUE_MASK) : 0ull);
+            break;
+        }
+        prefix += warp_sum_u64(v & LB_VALUE_MASK);
+        j -= 32;
     }
-    st_release_u64(&status[b], LB_PREFIX | (prefix + agg));
+    if (__any_sync(FULL, timed_out) && lane == 0) atomicOr(err, DEV_ERR_TIMEOUT);
+    if (lane == 0) st_release_u64(&status[b], LB_PREFIX | (prefix + agg));
     return (int64_t)prefix;
 }
 
-// Thread 0: publish this bin's merged count, find its prefix, check C's
-// capacity, and let the last bin write nnz(C) and the final row pointer.
+// Decoupled look-back by the whole CTA: thread t inspects bin j - t, so one
+// round covers THREADS predecessors.  A round is accepted when every bin
+// closer than the nearest inclusive prefix has published its count; the
+// counts up to that prefix are then summed.  Returns the exclusive prefix
+// (all threads); thread 0 publishes this bin's aggregate and inclusive prefix.
+template <int THREADS>
+__device__ inline int64_t lookback_block(uint64_t *status, int64_t b, uint64_t agg, uint32_t *err, int64_t *scratch,
+                                         int32_t *marks) {
+    const int tid = threadIdx.x;
+    if (b == 0) {
+        if (tid == 0) st_release_u64(&status[0], LB_PREFIX | agg);
+        return 0;
+    }
+    if (tid == 0) st_release_u64(&status[b], LB_AGGREGATE | agg);
+    uint64_t prefix = 0;
+    int64_t j = b - 1;
+    uint32_t rounds = 0;
+    while (true) {
+        const int64_t idx = j - tid;
+        const uint64_t v = (idx >= 0) ? ld_acquire_u64(&status[idx]) : LB_PREFIX;  // before bin 0: prefix 0
+        if (tid == 0) {
+            marks[0] = THREADS;  // nearest inclusive prefix
+            marks[1] = THREADS;  // nearest unpublished bin
+        }
+        __syncthreads();
+        if ((v & ~LB_VALUE_MASK) == LB_PREFIX) atomicMin(&marks[0], tid);
+        if ((v >> LB_FLAG_SHIFT) == 0) atomicMin(&marks[1], tid);
+        __syncthreads();
+        const int fp = marks[0], fz = marks[1];
+        if (fz < fp) {  // a bin in front of the nearest prefix has not published yet: poll again
+            if (++rounds > SPIN_LIMIT) {
+                if (tid == 0) atomicOr(err, DEV_ERR_TIMEOUT);
+                break;  // give up: keep the partial sum so the chain keeps moving
+            }
+            __nanosleep(64);
+            __syncthreads();
+            continue;
+        }
+        const uint64_t mine = (tid <= fp) ? (v & LB_VALUE_MASK) : 0ull;
+        prefix += (uint64_t)block_reduce_sum<int64_t, THREADS>((int64_t)mine, scratch);
+        if (fp < THREADS) break;
+        j -= THREADS;
+    }
+    if (tid == 0) st_release_u64(&status[b], LB_PREFIX | (prefix + agg));
+    return (int64_t)prefix;
+}
+
+// Warp 0: publish this bin's merged count, find its prefix, check C's capacity,
+// and let the last bin write nnz(C) and the final row pointer.
 __device__ inline void publish_and_check(const NumericArgs &p, int64_t b, int64_t U, int64_t *prefix, int32_t *ok) {
-    const int64_t P = lookback(p.status, b, (uint64_t)U, p.err);
+    const int64_t P = lookback_warp(p.status, b, (uint64_t)U, p.err);
+    if ((threadIdx.x & 31) != 0) return;
     *prefix = P;
     int32_t good = p.count_only ? 0 : 1;
     if (!p.count_only && (P + U > p.cap || (p.rowptr32 && P + U > 0x7fffffffll))) {
@@ -133,7 +243,7 @@ __device__ void stream_oversize_bin(const NumericArgs &p, int64_t b, int32_t row
     const TV *v = in_scratch ? static_cast<const TV *>(p.svals) + p.over_tuple_off[o]
                              : static_cast<const TV *>(p.vals) + off;
     OV *valC = static_cast<OV *>(p.valC);
-    if (tid == 0) publish_and_check(p, b, p.over_u[o], prefix, okp);
+    if (tid < 32) publish_and_check(p, b, p.over_u[o], prefix, okp);
     __syncthreads();
     const int64_t P = *prefix;
     const bool ok = *okp != 0;
@@ -159,12 +269,14 @@ __device__ void stream_oversize_bin(const NumericArgs &p, int64_t b, int32_t row
 }
 
 template <int CAP, int THREADS, class TV, class OV>
-__global__ void __launch_bounds__(THREADS, (CAP <= 4096 ? 2 : 1)) k_binsort(const NumericArgs p) {
+__global__ void __launch_bounds__(THREADS, (THREADS <= 256 ? 4 : (THREADS <= 512 ? 2 : 1))) k_binsort(const NumericArgs p) {
     using S = SortSmem<CAP, THREADS, TV>;
     constexpr int NW = THREADS / 32;
-    constexpr int E = CAP / THREADS;  // items per thread
-    constexpr int WS = CAP / NW;      // positions per warp in the LSD pass
+    constexpr int E = CAP / THREADS;  // tuples per thread; also buckets per thread
+    constexpr int WS = CAP / NW;      // positions per warp in the LSD ranking
+    constexpr int LOG_CAP = (CAP == 2048) ? 11 : (CAP == 4096) ? 12 : 13;
     static_assert(WS % 32 == 0 && WS / 32 == E, "layout");
+    static_assert((1 << LOG_CAP) == CAP, "capacity");
     extern __shared__ __align__(128) unsigned char smem_raw[];
     S &sm = *reinterpret_cast<S *>(smem_raw);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -191,115 +303,88 @@ __global__ void __launch_bounds__(THREADS, (CAP <= 4096 ? 2 : 1)) k_binsort(cons
             continue;
         }
         int N = (int)Nfull;
+        const int rows_b = row1 - row0;
+        // ---- load the bin (bulk copies, 16-byte granules) -----------------------
         bool loaded = true;
-        // ---- load the bin (bulk copies, 16-byte granules) -------------------
-        if (N > 0) {
+        if (N > 0 && tid == 0) {
             const uint32_t n4 = (uint32_t)((N + 3) & ~3);
-            if (tid == 0) {
-                mbar_arrive_expect_tx(&sm.bar, n4 * 4u + n4 * (uint32_t)sizeof(TV));
-                bulk_g2s(sm.kin, p.keys + off, n4 * 4u, &sm.bar);
-                bulk_g2s(sm.vin, gvals + off, n4 * (uint32_t)sizeof(TV), &sm.bar);
-            }
+            mbar_arrive_expect_tx(&sm.bar, n4 * 4u + n4 * (uint32_t)sizeof(TV));
+            bulk_g2s(sm.kin, p.keys + off, n4 * 4u, &sm.bar);
+            bulk_g2s(sm.vin, gvals + off, n4 * (uint32_t)sizeof(TV), &sm.bar);
+        }
+        for (int r = tid; r < rows_b; r += THREADS) sm.rowcnt[r] = 0;
+        for (int i = tid; i <= CAP; i += THREADS) sm.cnt[i] = 0;
+        if (tid == 0) sm.big = 0;
+        if (N > 0) {
             loaded = mbar_wait_bounded(&sm.bar, phase);
             phase ^= 1u;
-            if (!loaded) {
-                if (tid == 0) atomicOr(p.err, DEV_ERR_TIMEOUT);
-                N = 0;
-            }
         }
         if (!__syncthreads_and(loaded)) {
+            if (tid == 0) atomicOr(p.err, DEV_ERR_TIMEOUT);
             // a bulk copy may still be landing: wait for it (bounded) before the buffer is reused
             (void)mbar_wait_bounded(&sm.bar, phase ^ 1u);
             N = 0;
         }
-        const int rows_b = row1 - row0;
+
         const uint32_t *sk = sm.skey;
         const uint16_t *si = sm.sidx;
-
         if (N > 0) {
-            // ---- key range ----------------------------------------------------
-            uint32_t kr[E];
-            uint32_t lmin = 0xffffffffu, lmax = 0;
-#pragma unroll
-            for (int j = 0; j < E; ++j) {
-                const int q = tid + j * THREADS;
-                kr[j] = (q < N) ? sm.kin[q] : 0u;
-                if (q < N) {
-                    lmin = min(lmin, kr[j]);
-                    lmax = max(lmax, kr[j]);
-                }
-            }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                lmin = min(lmin, __shfl_xor_sync(FULL, lmin, o));
-                lmax = max(lmax, __shfl_xor_sync(FULL, lmax, o));
-            }
-            if (tid == 0) {
-                sm.kmin = 0xffffffffu;
-                sm.kmax = 0;
-                sm.maxb = 0;
-            }
-            __syncthreads();
-            if (lane == 0) {
-                atomicMin(&sm.kmin, lmin);
-                atomicMax(&sm.kmax, lmax);
-            }
-            __syncthreads();
-            const uint32_t kmin = sm.kmin;
-            const uint32_t range = sm.kmax - kmin;
-            const int rbits = range ? 32 - __clz(range) : 0;
-            const int nbits = (N > 1) ? 32 - __clz((uint32_t)(N - 1)) : 0;
-            const int shift = rbits > nbits ? rbits - nbits : 0;
-            const int nbk = (int)(range >> shift) + 1;  // <= 2^nbits <= CAP
-            // ---- bucket pass (MSD on the top bits) ------------------------------
-            for (int i = tid; i < nbk; i += THREADS) sm.cnt[i] = 0;
-            __syncthreads();
-            uint32_t rk[E];
-            uint32_t lmaxb = 0;
+            // Keys lie in [0, rows_b << colbits): the bucket of a key is its top
+            // LOG_CAP significant bits.
+            const uint32_t kmax = (uint32_t)((((uint64_t)rows_b) << p.colbits) - 1u);
+            const int rbits = kmax ? 32 - __clz(kmax) : 0;
+            const int shift = rbits > LOG_CAP ? rbits - LOG_CAP : 0;
+            // ---- bucket pass (MSD on the top bits) -----------------------------------
+            uint32_t kr[E], rk[E];
+            bool mine_big = false;
 #pragma unroll
             for (int j = 0; j < E; ++j) {
                 const int q = tid + j * THREADS;
                 if (q < N) {
-                    rk[j] = atomicAdd(&sm.cnt[(kr[j] - kmin) >> shift], 1u);
-                    lmaxb = max(lmaxb, rk[j] + 1u);
+                    kr[j] = sm.kin[q];
+                    rk[j] = atomicAdd(&sm.cnt[kr[j] >> shift], 1u);
+                    mine_big |= rk[j] >= SMALL_BUCKET;
                 }
             }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) lmaxb = max(lmaxb, __shfl_xor_sync(FULL, lmaxb, o));
-            if (lane == 0) atomicMax(&sm.maxb, lmaxb);
+            if (mine_big) sm.big = 1;
             __syncthreads();
-            const bool small = sm.maxb <= SMALL_BUCKET;
-            if (small) {
-                smem_exclusive_scan<THREADS>(sm.cnt, nbk, sm.scratch);
+            if (sm.big == 0) {
+                smem_exclusive_scan_striped<THREADS, CAP / THREADS>(sm.cnt, sm.scratch);
+                if (tid == 0) sm.cnt[CAP] = N;
 #pragma unroll
                 for (int j = 0; j < E; ++j) {
                     const int q = tid + j * THREADS;
                     if (q < N) {
-                        const uint32_t pos = sm.cnt[(kr[j] - kmin) >> shift] + rk[j];
+                        const uint32_t pos = sm.cnt[kr[j] >> shift] + rk[j];
                         sm.skey[pos] = kr[j];
                         sm.sidx[pos] = (uint16_t)q;
                     }
                 }
                 __syncthreads();
-                for (int bk = tid; bk < nbk; bk += THREADS) {
-                    const int lo = (int)sm.cnt[bk];
-                    const int hi = (bk + 1 < nbk) ? (int)sm.cnt[bk + 1] : N;
-                    for (int i = lo + 1; i < hi; ++i) {
-                        const uint32_t kk = sm.skey[i];
-                        const uint16_t xx = sm.sidx[i];
-                        int jj = i - 1;
-                        while (jj >= lo && sm.skey[jj] > kk) {
-                            sm.skey[jj + 1] = sm.skey[jj];
-                            sm.sidx[jj + 1] = sm.sidx[jj];
-                            --jj;
+                // Each tuple's final slot: its bucket's start plus the number of
+                // tuples of the same bucket with a smaller key (ties by position).
+                // Buckets hold a few tuples, so this is a short loop per tuple.
+#pragma unroll
+                for (int j = 0; j < E; ++j) {
+                    const int q = tid + j * THREADS;
+                    if (q < N) {
+                        const uint32_t key = sm.skey[q];
+                        const uint32_t bk = key >> shift;
+                        const int lo = (int)sm.cnt[bk], hi = (int)sm.cnt[bk + 1];
+                        int rank = lo;
+                        for (int r = lo; r < hi; ++r) {
+                            const uint32_t o = sm.skey[r];
+                            rank += (o < key) || (o == key && r < q);
                         }
-                        sm.skey[jj + 1] = kk;
-                        sm.sidx[jj + 1] = xx;
+                        sm.kin[rank] = key;
+                        sm.sidx2[rank] = sm.sidx[q];
                     }
                 }
                 __syncthreads();
+                sk = sm.kin;
+                si = sm.sidx2;
             } else {
-                // ---- stable LSD radix sort, 8-bit digits ---------------------------
+                // ---- stable LSD radix sort, 8-bit digits ---------------------------------
                 uint32_t *srck = sm.kin;
                 const uint16_t *srci = nullptr;  // identity on the first pass
                 uint32_t *dstk = sm.skey;
@@ -316,7 +401,7 @@ __global__ void __launch_bounds__(THREADS, (CAP <= 4096 ? 2 : 1)) k_binsort(cons
                         const int q = warp * WS + j * 32 + lane;
                         const bool valid = q < N;
                         const uint32_t key = valid ? srck[q] : 0u;
-                        const uint32_t d = ((key - kmin) >> sh) & 255u;
+                        const uint32_t d = (key >> sh) & 255u;
                         uint32_t peers = __ballot_sync(FULL, valid);
 #pragma unroll
                         for (int bit = 0; bit < 8; ++bit) {
@@ -349,7 +434,6 @@ __global__ void __launch_bounds__(THREADS, (CAP <= 4096 ? 2 : 1)) k_binsort(cons
                         }
                     }
                     __syncthreads();
-                    // next pass reads what this pass wrote
                     srck = dstk;
                     srci = dsti;
                     dstk = (dstk == sm.skey) ? sm.kin : sm.skey;
@@ -359,44 +443,75 @@ __global__ void __launch_bounds__(THREADS, (CAP <= 4096 ? 2 : 1)) k_binsort(cons
                 si = srci;
             }
         }
-
-        // ---- compress: count merged entries, per-row counts ----------------------
-        for (int r = tid; r < rows_b; r += THREADS) sm.cnt[r] = 0;
+        // ---- compress: each warp counts the merged entries of its segment ------------
+        const int seg = ((((N + NW - 1) / NW) + 31) / 32) * 32;
+        const int s0 = min(warp * seg, N), s1 = min(s0 + seg, N);
+        uint32_t wheads = 0;
+        for (int base = s0; base < s1; base += 32) {
+            const int q = base + lane;
+            const bool head = q < s1 && (q == 0 || sk[q - 1] != sk[q]);
+            wheads += __popc(__ballot_sync(FULL, head));
+            if (head) atomicAdd(&sm.rowcnt[sk[q] >> p.colbits], 1u);
+        }
+        if (lane == 0) sm.wtot[warp] = wheads;
         __syncthreads();
-        int64_t local_u = 0;
-        for (int q = tid; q < N; q += THREADS) {
-            const uint32_t key = sk[q];
-            if (q == 0 || sk[q - 1] != key) {
-                ++local_u;
-                atomicAdd(&sm.cnt[key >> p.colbits], 1u);
+        int64_t U = 0, wbase = 0;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) {
+            const uint32_t t = sm.wtot[w];
+            wbase += (w < warp) ? t : 0;
+            U += t;
+        }
+        {
+            const int64_t P = lookback_block<THREADS>(p.status, b, (uint64_t)U, p.err, sm.scratch, sm.marks);
+            if (tid == 0) {
+                int32_t good = p.count_only ? 0 : 1;
+                if (!p.count_only && (P + U > p.cap || (p.rowptr32 && P + U > 0x7fffffffll))) {
+                    atomicOr(p.err, DEV_ERR_OVERFLOW);
+                    good = 0;
+                }
+                sm.prefix = P;
+                sm.ok = good;
+                if (b == p.nbins - 1) {
+                    if (good) write_rowptr(p, p.m, P + U);
+                    if (p.nnz_dev) *p.nnz_dev = P + U;
+                }
+            }
+            __syncthreads();
+        }
+        if (warp == 0) {
+            // row pointers of this bin's rows: exclusive scan of the per-row counts
+            if (sm.ok) {
+                const int64_t P = sm.prefix;
+                uint32_t carry = 0;
+                for (int r0 = 0; r0 < rows_b; r0 += 32) {
+                    const int r = r0 + lane;
+                    const uint32_t c = (r < rows_b) ? sm.rowcnt[r] : 0u;
+                    const uint32_t inc = warp_inclusive_scan(c);
+                    if (r < rows_b) write_rowptr(p, row0 + r, P + carry + inc - c);
+                    carry += __shfl_sync(FULL, inc, 31);
+                }
             }
         }
-        const int64_t U = block_reduce_sum<int64_t, THREADS>(local_u, sm.scratch);
-        if (tid == 0) publish_and_check(p, b, U, &sm.prefix, &sm.ok);
         __syncthreads();
         const int64_t P = sm.prefix;
-        const bool ok = sm.ok != 0;
-        // ---- row pointers of this bin's rows -----------------------------------
-        smem_exclusive_scan<THREADS>(sm.cnt, rows_b, sm.scratch);
-        if (ok)
-            for (int r = tid; r < rows_b; r += THREADS) write_rowptr(p, row0 + r, P + sm.cnt[r]);
-        // ---- merged entries in key order ---------------------------------------
-        int64_t running = 0;
-        for (int base = 0; base < N; base += THREADS) {
-            const int q = base + tid;
-            const bool valid = q < N;
-            const uint32_t key = valid ? sk[q] : 0u;
-            const bool head = valid && (q == 0 || sk[q - 1] != key);
-            int64_t chunk_total;
-            const int64_t u = block_exclusive_scan<int64_t, THREADS>(head ? 1 : 0, sm.scratch, &chunk_total);
-            if (head && ok) {
-                double acc = (double)sm.vin[si[q]];
-                for (int r = q + 1; r < N && sk[r] == key; ++r) acc += (double)sm.vin[si[r]];
-                const int64_t out = P + running + u;
-                p.colidx[out] = (int32_t)(key & colmask);
-                valC[out] = (OV)acc;
+        if (sm.ok) {
+            // ---- merged entries in key order, coalesced across the warp ----------------
+            int64_t out = P + wbase;
+            for (int base = s0; base < s1; base += 32) {
+                const int q = base + lane;
+                const bool head = q < s1 && (q == 0 || sk[q - 1] != sk[q]);
+                const uint32_t hm = __ballot_sync(FULL, head);
+                if (head) {
+                    const uint32_t key = sk[q];
+                    double acc = (double)sm.vin[si[q]];
+                    for (int r = q + 1; r < N && sk[r] == key; ++r) acc += (double)sm.vin[si[r]];
+                    const int64_t o = out + __popc(hm & lanemask_lt());
+                    p.colidx[o] = (int32_t)(key & colmask);
+                    valC[o] = (OV)acc;
+                }
+                out += __popc(hm);
             }
-            running += chunk_total;
         }
         __syncthreads();
     }
@@ -424,16 +539,14 @@ cudaError_t run_binsort(const NumericArgs &a, cudaStream_t s) {
 template <class TV, class OV>
 cudaError_t dispatch_cap(const NumericArgs &a, cudaStream_t s) {
     switch (a.capacity) {
-        case 2048: return run_binsort<2048, 512, TV, OV>(a, s);
+        case 2048: return run_binsort<2048, 256, TV, OV>(a, s);
         case 4096: return run_binsort<4096, 512, TV, OV>(a, s);
-        case 8192: return run_binsort<8192, 512, TV, OV>(a, s);
+        case 8192: return run_binsort<8192, 1024, TV, OV>(a, s);
         default: return cudaErrorInvalidValue;
     }
 }
 
 }  // namespace
-
-int binsort_max_capacity(int dtype) { return dtype == PB_F64 ? 8192 : 8192; }
 
 cudaError_t launch_binsort(const NumericArgs &a, cudaStream_t s) {
     if (a.nbins <= 0) return cudaSuccess;

@@ -30,6 +30,10 @@ constexpr uint32_t SPIN_LIMIT = 1u << 24;
 // Tuples per work item of the oversize-bin sort.
 constexpr int OVER_CHUNK = 4096;
 
+// A bin spans at most 2^RMAX_LOG2 rows (fewer when the column bits leave less
+// room in the 32-bit key).
+constexpr int RMAX_LOG2 = 11;
+
 // Plan header filled on the device by the symbolic phase, read back once.
 struct PlanHeader {
     int64_t flop;
@@ -50,6 +54,8 @@ struct SymbolicArgs {
     int64_t *R;          // [m+1]
     int64_t *flags;      // [m+1] scratch: bin-start flags, then their exclusive scan
     uint64_t *rowinfo;   // [m]   (bin << 32) | (local_row << colbits)
+    uint64_t *ainfo;     // [nnzA] rowinfo of each A entry's row
+    int64_t nnzA;
     int32_t *bin_row;    // [m+2]
     int64_t *bin_off;    // [m+2]
     PlanHeader *hdr;
@@ -203,7 +209,8 @@ void count_launches(int64_t n);
 
 // Kernel launchers implemented in the other translation units.
 cudaError_t launch_symbolic(const SymbolicArgs &a, int64_t *scan_tmp, cudaStream_t s);
-cudaError_t launch_chunk_table(const int64_t *F, int32_t k, int64_t flop, int64_t chunk, int32_t *chunk_k,
+cudaError_t launch_chunk_table(const int64_t *F, const int32_t *colptrA, const int32_t *rowptrB, int32_t k,
+                               int64_t nnzA, int64_t nchunks, int64_t chunk, int32_t *chunk_e, int32_t *acol,
                                cudaStream_t s);
 cudaError_t launch_over_chunk_map(const int64_t *over_chunk_off, int64_t n_over, int32_t *over_chunk_bin,
                                   cudaStream_t s);
@@ -216,17 +223,18 @@ struct NumericArgs {
     const void *valA, *valB;
     // plan
     const int64_t *F, *R;
-    const uint64_t *rowinfo;
+    const uint64_t *ainfo;  // [nnzA] bin << 32 | key high part, per A entry
+    const int32_t *acol;    // [nnzA] column of each A entry
     const int32_t *bin_row;
     const int64_t *bin_off;
-    const int32_t *chunk_k;
+    const int32_t *chunk_e; // [nchunks+1] first A entry of each expand work item
     int64_t flop, nbins, nchunks, chunk;
     int32_t colbits;
     int32_t capacity;
     // workspace
     uint32_t *keys;
     void *vals;
-    uint32_t *cursor;    // [nbins]
+    uint64_t *cursor;    // [nbins] next free absolute slot of each bin
     uint64_t *status;    // [nbins] look-back words
     uint32_t *ticket;    // [1]
     uint32_t *err;       // [1] device status word
@@ -249,6 +257,7 @@ struct NumericArgs {
 };
 
 cudaError_t launch_expand(const NumericArgs &a, cudaStream_t s);
+
 cudaError_t launch_binsort(const NumericArgs &a, cudaStream_t s);
 int binsort_max_capacity(int dtype);
 

@@ -1,32 +1,72 @@
 // Expand phase with propagation blocking (Alg. 2 expand loop, Sec. III-C).
 //
-// The flop tuples are enumerated in the order of Alg. 2: column k of A (and
-// row k of B), then each (rowid, aval) of A(:,k), then each (colid, bval) of
-// B(k,:).  Tuple t lies in column k with F[k] <= t < F[k+1]; inside it,
-// u = t - F[k] selects A entry u / nnz(B(k,:)) and B entry u % nnz(B(k,:)).
+// Alg. 2 walks column k of A (and row k of B), each (rowid, aval) of A(:,k)
+// and each (colid, bval) of B(k,:), emitting (rowid, colid, aval*bval).  The
+// tuples of one A entry form a run of nnz(B(k,:)) tuples, all for the same
+// row, hence the same bin.
 //
-// Work split: the tuple range is cut into equal chunks (flop-balanced, not
-// column-balanced, so hub columns of skewed inputs spread over many warps).
-// A warp walks its chunk 32 tuples at a time.  For each group of 32 it loads
-// the end offsets F[k+1] of the next 32 columns into the lanes once, and each
-// lane finds its column with a 5-step shuffle search.
-//
+// Work split: expand work items are ranges of A entries (CSC order) holding
+// about `chunk` tuples each (flop-balanced, so hub columns of skewed inputs
+// spread over many warps).  A warp takes 32 consecutive A entries at a time,
+// one per lane:
+//   1. each lane loads its entry's column, bin info and value and the extent
+//      of B(k,:), then reserves its whole run in its bin with one atomic on
+//      the bin's cursor (32 independent reservations in flight per warp);
+//   2. runs shorter than 32 tuples are written as one flattened stream: lane
+//      l of step s handles tuple 32s + l of the concatenated runs, found by a
+//      shuffle search over the runs' prefix sums, so consecutive lanes write
+//      consecutive slots of the same run;
+//   3. runs of 32 or more tuples are written one at a time by the whole warp.
 // Propagation blocking: tuple (i, j, a*b) goes to the bin holding row i (row
 // ranges from the symbolic phase) as key = (i - first row of bin) << colbits | j
-// and value a*b.  All B entries produced by one A entry share a bin, and such
-// runs occupy consecutive lanes, so one lane per run reserves the whole run
-// with a single atomic on the bin's cursor and the run is written to
-// consecutive slots (warp-aggregated offsets; the writes of a run are
-// contiguous 4-byte keys and 8-byte values).
+// and value a*b.  Reserving at a bin's cursor appends at the bin's frontier,
+// so partially written sectors stay few and L2-resident until completed.
 #include "pb_common.cuh"
 
 namespace pb {
 
 namespace {
 
+constexpr int LONG_RUN = 32;
+
 template <class TV, class IV>
 __device__ inline TV tuple_product(IV a, IV b) {
     return static_cast<TV>(a * b);
+}
+
+// Reserve `len` slots of `bin`; returns the first absolute position or -1.
+__device__ inline int64_t reserve(const NumericArgs &p, uint32_t bin, uint32_t len) {
+    const int64_t pos = (int64_t)atomicAdd(reinterpret_cast<unsigned long long *>(&p.cursor[bin]),
+                                           (unsigned long long)len);
+    if (pos + len > p.bin_off[bin + 1]) {  // operands differ from the plan's structure
+        atomicOr(p.err, DEV_ERR_CAPACITY);
+        return -1;
+    }
+    return pos;
+}
+
+template <class IV>
+struct Batch {  // one A entry per lane
+    uint64_t info;
+    IV av;
+    int32_t b0, lb;
+};
+
+template <class IV>
+__device__ inline Batch<IV> load_batch(const NumericArgs &p, const IV *__restrict__ valA, int32_t e, bool valid) {
+    Batch<IV> x;
+    x.info = 0;
+    x.av = IV(0);
+    x.b0 = 0;
+    x.lb = 0;
+    if (valid) {
+        const int32_t k = p.acol[e];
+        x.info = p.ainfo[e];
+        x.av = valA[e];
+        x.b0 = p.rowptrB[k];
+        x.lb = p.rowptrB[k + 1] - x.b0;
+    }
+    return x;
 }
 
 template <class IV, class TV>
@@ -36,87 +76,68 @@ __global__ void __launch_bounds__(256) k_expand(const NumericArgs p) {
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const IV *__restrict__ valA = static_cast<const IV *>(p.valA);
     const IV *__restrict__ valB = static_cast<const IV *>(p.valB);
+    const int32_t *__restrict__ colidxB = p.colidxB;
+    uint32_t *__restrict__ keys = p.keys;
     TV *__restrict__ vals = static_cast<TV *>(p.vals);
 
     for (int64_t c = gwarp; c < p.nchunks; c += nwarps) {
-        int64_t t = c * p.chunk;
-        const int64_t tend = min(t + p.chunk, p.flop);
-        int32_t kc = p.chunk_k[c];
-        while (t < tend) {
-            // Frontier: columns kc .. kc+31, one per lane.
-            const int32_t kk = kc + lane;
-            int64_t fend = INT64_MAX;
-            int32_t a0 = 0, b0 = 0, lb = 1;
-            if (kk < p.k) {
-                fend = p.F[kk + 1];
-                a0 = p.colptrA[kk];
-                b0 = p.rowptrB[kk];
-                lb = p.rowptrB[kk + 1] - b0;
-            }
-            int64_t fbeg = __shfl_up_sync(FULL, fend, 1);
-            if (lane == 0) fbeg = p.F[kc];
-            const int64_t span = min(tend, __shfl_sync(FULL, fend, 31));
-            for (int64_t base = t; base < span; base += 32) {
-                const int64_t tt = base + lane;
-                const bool act = tt < span;  // active lanes form a prefix of the warp
-                int l = 0;
+        const int32_t e_begin = p.chunk_e[c], e_end = p.chunk_e[c + 1];
+        Batch<IV> cur = load_batch(p, valA, e_begin + lane, e_begin + lane < e_end);
+        for (int32_t e0 = e_begin; e0 < e_end; e0 += 32) {
+            const bool valid = e0 + lane < e_end;
+            const bool is_long = cur.lb >= LONG_RUN;
+            const int32_t sl = is_long ? 0 : cur.lb;
+            int64_t pos = -1;
+            if (sl > 0) pos = reserve(p, (uint32_t)(cur.info >> 32), (uint32_t)sl);
+            // software pipeline: the next batch's loads overlap this batch's reservations and writes
+            const int32_t en = e0 + 32 + lane;
+            const Batch<IV> nxt = load_batch(p, valA, en, en < e_end);
+            // ---- short runs as one flattened stream --------------------------------
+            const int32_t incl = warp_inclusive_scan(sl);
+            const int32_t total = __shfl_sync(FULL, incl, 31);
+            for (int32_t t0 = 0; t0 < total; t0 += 32) {
+                const int32_t t = t0 + lane;
+                int r = 0;  // the run holding tuple t: number of runs ending at or before t
 #pragma unroll
-                for (int s = 16; s >= 1; s >>= 1) {
-                    int64_t f = __shfl_sync(FULL, fend, l + s - 1);
-                    if (f <= tt) l += s;
-                }
-                const int64_t fk = __shfl_sync(FULL, fbeg, l);
-                const int32_t A0 = __shfl_sync(FULL, a0, l);
-                const int32_t B0 = __shfl_sync(FULL, b0, l);
-                const int32_t LB = __shfl_sync(FULL, lb, l);
-                int32_t ea = -1, eb = 0;
+                for (int s = 16; s >= 1; s >>= 1)
+                    if (__shfl_sync(FULL, incl, r + s - 1) <= t) r += s;
+                const int32_t ib = t - (__shfl_sync(FULL, incl, r) - __shfl_sync(FULL, sl, r));
+                const int32_t br = __shfl_sync(FULL, cur.b0, r);
+                const uint32_t keyhi = (uint32_t)__shfl_sync(FULL, (uint32_t)cur.info, r);
+                const IV ar = __shfl_sync(FULL, cur.av, r);
+                const bool act = t < total;
+                uint32_t col = 0;
+                IV bv = IV(0);
                 if (act) {
-                    const int64_t u = tt - fk;
-                    int64_t ia;
-                    if ((u >> 32) == 0)
-                        ia = (uint32_t)u / (uint32_t)LB;
-                    else
-                        ia = u / LB;
-                    ea = A0 + (int32_t)ia;
-                    eb = B0 + (int32_t)(u - ia * LB);
+                    col = (uint32_t)colidxB[br + ib];
+                    bv = valB[br + ib];
                 }
-                // Runs of lanes sharing one A entry share one bin.
-                const int32_t prev = __shfl_up_sync(FULL, ea, 1);
-                const bool head = act && (lane == 0 || prev != ea);
-                const uint32_t heads = __ballot_sync(FULL, head);
-                const uint32_t actmask = __ballot_sync(FULL, act);
-                if (act) {
-                    const int32_t row = p.rowidxA[ea];
-                    const IV av = valA[ea];
-                    const int32_t col = p.colidxB[eb];
-                    const IV bv = valB[eb];
-                    const uint64_t info = p.rowinfo[row];
-                    const uint32_t bin = (uint32_t)(info >> 32);
-                    const uint32_t key = (uint32_t)info | (uint32_t)col;
-                    const uint32_t upto = heads & (FULL >> (31 - lane));   // heads at lanes <= mine
-                    const int sstart = 31 - __clz(upto);
-                    const uint32_t above = heads & ~(FULL >> (31 - lane)); // heads at lanes > mine
-                    const int send = above ? (__ffs(above) - 1) : (32 - __clz(actmask));
-                    int64_t pos = 0;
-                    if (head) {
-                        const uint32_t len = (uint32_t)(send - sstart);
-                        pos = p.bin_off[bin] + (int64_t)atomicAdd(&p.cursor[bin], len);
-                        // a run past the bin's slots means the operands differ from the plan
-                        if (pos + len > p.bin_off[bin + 1]) {
-                            atomicOr(p.err, DEV_ERR_CAPACITY);
-                            pos = -1;
-                        }
-                    }
-                    pos = __shfl_sync(actmask, pos, sstart);
-                    if (pos >= 0) {
-                        pos += lane - sstart;
-                        p.keys[pos] = key;
-                        vals[pos] = tuple_product<TV, IV>(av, bv);
-                    }
+                const int64_t pr = __shfl_sync(FULL, pos, r);
+                if (act && pr >= 0) {
+                    keys[pr + ib] = keyhi | col;
+                    vals[pr + ib] = tuple_product<TV, IV>(ar, bv);
                 }
             }
-            t = span;
-            kc += 32;
+            // ---- long runs, one per warp step -------------------------------------
+            uint32_t lm = __ballot_sync(FULL, valid && is_long);
+            while (lm) {
+                const int r = __ffs(lm) - 1;
+                lm &= lm - 1;
+                const uint64_t ir = __shfl_sync(FULL, cur.info, r);
+                const IV ar = __shfl_sync(FULL, cur.av, r);
+                const int32_t br = __shfl_sync(FULL, cur.b0, r);
+                const int32_t lr = __shfl_sync(FULL, cur.lb, r);
+                int64_t pr = 0;
+                if (lane == 0) pr = reserve(p, (uint32_t)(ir >> 32), (uint32_t)lr);
+                pr = __shfl_sync(FULL, pr, 0);
+                if (pr < 0) continue;
+                const uint32_t keyhi = (uint32_t)ir;
+                for (int32_t ib = lane; ib < lr; ib += 32) {
+                    keys[pr + ib] = keyhi | (uint32_t)colidxB[br + ib];
+                    vals[pr + ib] = tuple_product<TV, IV>(ar, valB[br + ib]);
+                }
+            }
+            cur = nxt;
         }
     }
 }

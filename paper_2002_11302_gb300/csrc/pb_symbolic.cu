@@ -138,6 +138,12 @@ __global__ void k_over_list(const int64_t *R, const int32_t *bin_row, int64_t ca
     }
 }
 
+// ainfo[e] = rowinfo[rowidxA[e]]: the bin and key high part of every A entry.
+__global__ void k_ainfo(int64_t nnz, const int32_t *rowidxA, const uint64_t *rowinfo, uint64_t *ainfo) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nnz; e += (int64_t)gridDim.x * blockDim.x)
+        ainfo[e] = rowinfo[rowidxA[e]];
+}
+
 __global__ void k_finish_header(const int64_t *F, int32_t k, int32_t m, const int64_t *bin_off,
                                 const int64_t *over_scan, const int64_t *over_chunk_off,
                                 const int64_t *over_tuple_off, PlanHeader *hdr) {
@@ -153,15 +159,30 @@ __global__ void k_over_chunk_map(const int64_t *over_chunk_off, int64_t n_over, 
         for (int64_t c = over_chunk_off[o]; c < over_chunk_off[o + 1]; ++c) over_chunk_bin[c] = (int32_t)o;
 }
 
-// Chunk table for the expand phase: chunk c starts at tuple c*chunk, which
-// lies in column k with F[k] <= c*chunk < F[k+1].
-__global__ void k_chunk_table(const int64_t *F, int32_t k, int64_t flop, int64_t chunk, int32_t *chunk_k) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < k; i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t lo = F[i], hi = F[i + 1];
-        if (hi <= lo) continue;
-        for (int64_t c = ceil_div<int64_t>(lo, chunk); c * chunk < hi && c * chunk < flop; ++c) chunk_k[c] = (int32_t)i;
+// Expand work items at A-entry granularity.  The runs of tuples of the A
+// entries tile [0, flop) in CSC order: entry j of column k owns
+// [F[k] + j*lb, F[k] + (j+1)*lb) with lb = nnz(B(k,:)).  Work item c holds the
+// entries whose run starts in [c*chunk, (c+1)*chunk): chunk_e[c] is the first
+// of them.  Also records the column of every A entry (acol).
+__global__ void k_chunk_table(const int64_t *F, const int32_t *colptrA, const int32_t *rowptrB, int32_t k,
+                              int64_t chunk, int32_t *chunk_e, int32_t *acol) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t col = warp; col < k; col += nwarps) {
+        const int32_t a0 = colptrA[col], la = colptrA[col + 1] - a0;
+        const int64_t lb = (int64_t)rowptrB[col + 1] - rowptrB[col];
+        for (int32_t j = lane; j < la; j += 32) {
+            const int32_t e = a0 + j;
+            acol[e] = (int32_t)col;
+            if (lb == 0) continue;
+            const int64_t s = F[col] + (int64_t)j * lb, r = s + lb;
+            for (int64_t c = ceil_div<int64_t>(s, chunk); c * chunk < r; ++c) chunk_e[c] = (c * chunk == s) ? e : e + 1;
+        }
     }
 }
+
+__global__ void k_set_i32(int32_t *p, int32_t v) { *p = v; }
 
 unsigned grid_for(int64_t n, int threads) {
     int64_t g = ceil_div<int64_t>(n > 0 ? n : 1, threads);
@@ -193,7 +214,9 @@ cudaError_t launch_symbolic(const SymbolicArgs &a, int64_t *scan_tmp, cudaStream
     if ((e = cudaMemsetAsync(a.bin_off, 0, sizeof(int64_t) * ((size_t)a.m + 2), s)) != cudaSuccess) return e;
     k_bin_sizes<<<grid_for(a.m, T), T, 0, s>>>(a.R, a.bin_row, a.capacity, a.hdr, a.bin_off);
     if ((e = scan_i64(a.bin_off, a.m, scan_tmp, s)) != cudaSuccess) return e;
-    // 5. oversize bins (single rows above the on-chip capacity): list, work items, scratch offsets
+    // 5. bin and key high part of every A entry
+    k_ainfo<<<grid_for(a.nnzA, T), T, 0, s>>>(a.nnzA, a.rowidxA, a.rowinfo, a.ainfo);
+    // 6. oversize bins (single rows above the on-chip capacity): list, work items, scratch offsets
     const size_t mb = sizeof(int64_t) * ((size_t)a.m + 1);
     if ((e = cudaMemsetAsync(a.over_scan, 0, mb, s)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(a.over_chunk_off, 0, mb, s)) != cudaSuccess) return e;
@@ -206,7 +229,7 @@ cudaError_t launch_symbolic(const SymbolicArgs &a, int64_t *scan_tmp, cudaStream
     if ((e = scan_i64(a.over_tuple_off, a.m, scan_tmp, s)) != cudaSuccess) return e;
     k_finish_header<<<1, 1, 0, s>>>(a.F, a.k, a.m, a.bin_off, a.over_scan, a.over_chunk_off, a.over_tuple_off,
                                     a.hdr);
-    count_launches(10);  // the non-scan kernels above
+    count_launches(11);  // the non-scan kernels above
     return cudaGetLastError();
 }
 
@@ -218,11 +241,16 @@ cudaError_t launch_over_chunk_map(const int64_t *over_chunk_off, int64_t n_over,
     return cudaGetLastError();
 }
 
-cudaError_t launch_chunk_table(const int64_t *F, int32_t k, int64_t flop, int64_t chunk, int32_t *chunk_k,
+cudaError_t launch_chunk_table(const int64_t *F, const int32_t *colptrA, const int32_t *rowptrB, int32_t k,
+                               int64_t nnzA, int64_t nchunks, int64_t chunk, int32_t *chunk_e, int32_t *acol,
                                cudaStream_t s) {
-    if (flop <= 0) return cudaSuccess;
-    k_chunk_table<<<grid_for(k, 256), 256, 0, s>>>(F, k, flop, chunk, chunk_k);
+    // chunk_e[nchunks] = nnzA closes the last work item
+    k_set_i32<<<1, 1, 0, s>>>(chunk_e + nchunks, (int32_t)nnzA);
     count_launches(1);
+    if (k > 0) {
+        k_chunk_table<<<grid_for((int64_t)k * 32, 256), 256, 0, s>>>(F, colptrA, rowptrB, k, chunk, chunk_e, acol);
+        count_launches(1);
+    }
     return cudaGetLastError();
 }
 
