@@ -181,25 +181,32 @@ __device__ inline int64_t lookback_block(uint64_t *status, int64_t b, uint64_t a
     if (tid == 0) st_release_u64(&status[b], LB_AGGREGATE | agg);
     uint64_t prefix = 0;
     int64_t j = b - 1;
-    uint32_t rounds = 0;
+    int64_t wait_for = b - 1;  // a bin whose count is needed and may be unpublished
     while (true) {
-        const int64_t idx = j - tid;
-        const uint64_t v = (idx >= 0) ? ld_acquire_u64(&status[idx]) : LB_PREFIX;  // before bin 0: prefix 0
+        // One lane waits (with backoff) until that bin has published; the other
+        // threads sleep at the barrier instead of polling.
         if (tid == 0) {
+            uint32_t spins = 0, ns = 32;
+            while ((ld_acquire_u64(&status[wait_for]) >> LB_FLAG_SHIFT) == 0) {
+                if (++spins > SPIN_LIMIT) {
+                    atomicOr(err, DEV_ERR_TIMEOUT);
+                    break;
+                }
+                __nanosleep(ns);
+                if (ns < 1024) ns <<= 1;
+            }
             marks[0] = THREADS;  // nearest inclusive prefix
             marks[1] = THREADS;  // nearest unpublished bin
         }
         __syncthreads();
+        const int64_t idx = j - tid;
+        const uint64_t v = (idx >= 0) ? ld_acquire_u64(&status[idx]) : LB_PREFIX;  // before bin 0: prefix 0
         if ((v & ~LB_VALUE_MASK) == LB_PREFIX) atomicMin(&marks[0], tid);
         if ((v >> LB_FLAG_SHIFT) == 0) atomicMin(&marks[1], tid);
         __syncthreads();
         const int fp = marks[0], fz = marks[1];
-        if (fz < fp) {  // a bin in front of the nearest prefix has not published yet: poll again
-            if (++rounds > SPIN_LIMIT) {
-                if (tid == 0) atomicOr(err, DEV_ERR_TIMEOUT);
-                break;  // give up: keep the partial sum so the chain keeps moving
-            }
-            __nanosleep(64);
+        if (fz < fp) {  // a bin in front of the nearest prefix has not published yet
+            wait_for = j - fz;
             __syncthreads();
             continue;
         }
@@ -207,6 +214,7 @@ __device__ inline int64_t lookback_block(uint64_t *status, int64_t b, uint64_t a
         prefix += (uint64_t)block_reduce_sum<int64_t, THREADS>((int64_t)mine, scratch);
         if (fp < THREADS) break;
         j -= THREADS;
+        wait_for = j;
     }
     if (tid == 0) st_release_u64(&status[b], LB_PREFIX | (prefix + agg));
     return (int64_t)prefix;
