@@ -190,6 +190,39 @@ pb_status pb_plan_destroy(pb_plan *plan);
 pb_status pb_set_phase_events(pb_handle *h, void *const *events);
 int64_t pb_kernel_launches(void);
 
+/*
+ * No-allocation entry point (the paper has no counterpart; this serves callers).
+ *
+ * Some callers cannot allocate device memory where they need a product: code
+ * whose device memory is owned by its own manager, latency-critical loops that
+ * must not enter an allocator, or callbacks that run while an allocation lock
+ * is held.  pb_spgemm_noalloc computes C = A * B (symbolic and numeric) using
+ * only a fixed scratch array of PB_NOALLOC_SCRATCH_BYTES bytes that the library
+ * defines in device memory; every GPU that loads the library holds that array
+ * until the process exits.  The call performs no cudaMalloc / cudaFree and no
+ * other allocation; the caller provides A, B and C exactly as for
+ * pb_spgemm_numeric (C->cap >= nnz(C); a capacity equal to the product's
+ * flop count, sum over k of nnz(A(:,k)) * nnz(B(k,:)), always suffices).
+ *
+ *   Limit: the plan arrays take about 84*A.nrows + 8*A.ncols + 12*nnz(A)
+ *   bytes and the tuples 12 (FP64) or 8 (FP32 forms) bytes each, all within
+ *   PB_NOALLOC_SCRATCH_BYTES; a larger product returns PB_ERR_WORKSPACE and
+ *   launches nothing further.
+ *   Synchronous: it synchronises `stream` (once after the symbolic phase and
+ *   once at the end) and stores the device-detected status (PB_OK,
+ *   PB_ERR_OVERFLOW, ...) in *device_status.
+ *   The first call on a device resolves the scratch array's device address
+ *   (cudaGetSymbolAddress, with that device current); make that first call
+ *   before any stream capture.
+ *   All calls share the one array and it keeps the last call's contents (the
+ *   call clears what it needs).  Calls whose work overlaps on the GPU, e.g.
+ *   issued on two streams, race on the array: serialise them.
+ * Errors: INVALID_ARG, SHAPE, UNSUPPORTED_DTYPE, UNSUPPORTED, WORKSPACE, CUDA.
+ */
+#define PB_NOALLOC_SCRATCH_BYTES (64u * 1024u * 1024u)
+pb_status pb_spgemm_noalloc(const pb_csc *A, const pb_csr *B, pb_dtype dtype, pb_csr_out *C, pb_stream_t stream,
+                            pb_status *device_status);
+
 #ifdef __cplusplus
 }
 #endif

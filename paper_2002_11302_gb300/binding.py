@@ -82,6 +82,8 @@ SIGNATURES = {
     "pb_plan_destroy": (ctypes.c_int, [_VP]),
     "pb_set_phase_events": (ctypes.c_int, [_VP, _VP]),
     "pb_kernel_launches": (_I64, []),
+    "pb_spgemm_noalloc": (ctypes.c_int, [ctypes.POINTER(_CSC), ctypes.POINTER(_CSR), ctypes.c_int,
+                                         ctypes.POINTER(_CSROut), _VP, ctypes.POINTER(ctypes.c_int)]),
 }
 
 _lib = None
@@ -312,6 +314,27 @@ def debug_expand(plan: Plan, A: CscMatrix, B: CsrMatrix, workspace: torch.Tensor
     _check(h.lib, h.ptr, h.lib.pb_debug_expand(h.ptr, plan.ptr, ctypes.byref(cA), ctypes.byref(cB),
                                                workspace.data_ptr(), workspace.numel(), _stream_ptr(stream)))
     return workspace, int(h.lib.pb_debug_values_offset(plan.ptr))
+
+
+def spgemm_noalloc(A: CscMatrix, B: CsrMatrix, C: CsrMatrix, dtype: int = PB_F64,
+                   nnz_out: Optional[torch.Tensor] = None, stream=None) -> int:
+    """C = A * B through pb_spgemm_noalloc (no device allocation by the library).
+
+    C must be sized by the caller (capacity = C.colidx.numel()).  Returns the
+    device-side status (0 = PB_OK); raises PBError for argument/size errors.
+    """
+    lib = load_library()
+    cA, cB = A._c(), B._c()
+    r64 = C.rowptr.data_ptr() if C.rowptr.dtype == torch.int64 else None
+    r32 = C.rowptr.data_ptr() if C.rowptr.dtype == torch.int32 else None
+    cC = _CSROut(C.nrows, C.ncols, C.colidx.numel(), r64, r32, C.colidx.data_ptr() or None,
+                 C.val.data_ptr() or None, nnz_out.data_ptr() if nnz_out is not None else None)
+    dev = ctypes.c_int()
+    st = lib.pb_spgemm_noalloc(ctypes.byref(cA), ctypes.byref(cB), dtype, ctypes.byref(cC), _stream_ptr(stream),
+                               ctypes.byref(dev))
+    if st != 0:
+        raise PBError(st, "pb_spgemm_noalloc")
+    return dev.value
 
 
 def alloc_output(plan: Plan, rowptr64: bool = True, cap: Optional[int] = None) -> CsrMatrix:
