@@ -97,7 +97,9 @@ typedef struct pb_config {
     int32_t sort_threads;    /* threads of one sort CTA (256 or 512)                           */
     int32_t expand_chunk;    /* tuples per expand work item                                     */
     int32_t reserved0;
-    int64_t max_tuple_bytes; /* cap on the tuple workspace; larger products run in row panels    */
+    int64_t max_tuple_bytes; /* cap on the tuple workspace (tuples plus the global-sort scratch of
+                                oversize rows); a larger product runs in row panels, consecutive
+                                bin ranges processed one after another                            */
     int64_t reserved1;
 } pb_config;
 

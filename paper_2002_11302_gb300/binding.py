@@ -307,6 +307,17 @@ def numeric(plan: Plan, A: CscMatrix, B: CsrMatrix, C: CsrMatrix, workspace: tor
                                                  _stream_ptr(stream)))
 
 
+def numeric_count(plan: Plan, A: CscMatrix, B: CsrMatrix, workspace: torch.Tensor, nnz_out: torch.Tensor,
+                  stream=None) -> None:
+    """Counting run: only nnz(C) is computed (into nnz_out), nothing is written to C."""
+    h = plan.handle
+    cA, cB = A._c(), B._c()
+    cC = _CSROut(plan.m, plan.n, 0, None, None, None, None, nnz_out.data_ptr())
+    _check(h.lib, h.ptr, h.lib.pb_spgemm_numeric(h.ptr, plan.ptr, ctypes.byref(cA), ctypes.byref(cB),
+                                                 ctypes.byref(cC), workspace.data_ptr(), workspace.numel(),
+                                                 _stream_ptr(stream)))
+
+
 def debug_expand(plan: Plan, A: CscMatrix, B: CsrMatrix, workspace: torch.Tensor, stream=None):
     """Run only the expand phase; returns (keys uint32-as-int32 view, values) views of the workspace."""
     h = plan.handle

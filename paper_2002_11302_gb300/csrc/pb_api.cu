@@ -1,10 +1,12 @@
 // Host side of the C ABI: handles, plans, argument checks, workspace layout
 // and the launch sequence of the symbolic and numeric phases.
+#include <algorithm>
 #include <atomic>
 #include <cstdio>
 #include <cstring>
 #include <new>
 #include <string>
+#include <vector>
 
 #include "pb_common.cuh"
 
@@ -26,8 +28,18 @@ static std::atomic<int64_t> g_launches{0};
 void count_launches(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 }  // namespace pb
 
+// A row panel: consecutive bins whose tuples fit the workspace together.
+struct pb_panel {
+    int64_t bin_lo, bin_hi;      // bins
+    int64_t tuple_base, tuples;  // padded tuple range [tuple_base, tuple_base + tuples)
+    int64_t o_lo, o_hi;          // oversize bins (indices into the oversize list)
+    int64_t c_lo, c_hi;          // their work items
+    int64_t over_base, over_tuples;
+};
+
 struct pb_plan {
     pb_handle *h = nullptr;
+    std::vector<pb_panel> panels;
     int32_t m = 0, k = 0, n = 0;
     int64_t nnzA = 0, nnzB = 0;
     pb_dtype dtype = PB_F64;
@@ -316,8 +328,76 @@ pb_status pb_spgemm_symbolic(pb_handle *h, const pb_csc *A, const pb_csr *B, pb_
         cuda_fail(h, e, "chunk table");
         return bail(PB_ERR_CUDA);
     }
-    // Workspace layout of the numeric phase.
-    const size_t T = (size_t)p->hdr.tuples_padded;
+    // Row panels: with a tuple budget smaller than the whole product, bins are
+    // grouped into consecutive panels whose tuples fit the budget together.
+    const size_t per_tuple = 4 + tuple_val_bytes(dtype);
+    const int64_t budget = (cfg && cfg->max_tuple_bytes > 0) ? cfg->max_tuple_bytes / (int64_t)per_tuple : 0;
+    if (budget > 0 && p->hdr.tuples_padded > budget) {
+        const size_t nb = (size_t)p->hdr.nbins, no = (size_t)p->hdr.n_oversize;
+        std::vector<int64_t> off(nb + 1), obin(no), ochunk(no + 1), otup(no + 1);
+        if ((e = cudaMemcpyAsync(off.data(), p->bin_off, 8 * (nb + 1), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+            (no && (e = cudaMemcpyAsync(obin.data(), p->over_bin, 8 * no, cudaMemcpyDeviceToHost, s)) != cudaSuccess) ||
+            (e = cudaMemcpyAsync(ochunk.data(), p->over_chunk_off, 8 * (no + 1), cudaMemcpyDeviceToHost, s)) !=
+                cudaSuccess ||
+            (e = cudaMemcpyAsync(otup.data(), p->over_tuple_off, 8 * (no + 1), cudaMemcpyDeviceToHost, s)) !=
+                cudaSuccess ||
+            (e = cudaStreamSynchronize(s)) != cudaSuccess) {
+            cuda_fail(h, e, "panel readback");
+            return bail(PB_ERR_CUDA);
+        }
+        // an oversize bin also needs its size again in scratch for its global sort
+        std::vector<char> is_over(nb, 0);
+        for (int64_t ob : obin) is_over[ob] = 1;
+        int64_t b = 0;
+        while (b < (int64_t)nb) {
+            pb_panel pn{};
+            pn.bin_lo = b;
+            int64_t used = 0;
+            while (b < (int64_t)nb) {
+                const int64_t cost = (off[b + 1] - off[b]) * (is_over[b] ? 2 : 1);
+                if (used + cost > budget) break;
+                used += cost;
+                ++b;
+            }
+            if (b == pn.bin_lo) {
+                fail(h, PB_ERR_WORKSPACE, "max_tuple_bytes is smaller than the largest bin");
+                return bail(PB_ERR_WORKSPACE);
+            }
+            pn.bin_hi = b;
+            p->panels.push_back(pn);
+        }
+        for (pb_panel &pn : p->panels) {
+            pn.tuple_base = off[pn.bin_lo];
+            pn.tuples = off[pn.bin_hi] - off[pn.bin_lo];
+            pn.o_lo = std::lower_bound(obin.begin(), obin.end(), pn.bin_lo) - obin.begin();
+            pn.o_hi = std::lower_bound(obin.begin(), obin.end(), pn.bin_hi) - obin.begin();
+            pn.c_lo = ochunk[pn.o_lo];
+            pn.c_hi = ochunk[pn.o_hi];
+            pn.over_base = otup[pn.o_lo];
+            pn.over_tuples = otup[pn.o_hi] - otup[pn.o_lo];
+        }
+    } else {
+        pb_panel pn{};
+        pn.bin_lo = 0;
+        pn.bin_hi = p->hdr.nbins;
+        pn.tuple_base = 0;
+        pn.tuples = p->hdr.tuples_padded;
+        pn.o_lo = 0;
+        pn.o_hi = p->hdr.n_oversize;
+        pn.c_lo = 0;
+        pn.c_hi = p->hdr.over_chunks;
+        pn.over_base = 0;
+        pn.over_tuples = p->hdr.over_tuples;
+        p->panels.push_back(pn);
+    }
+    int64_t max_t = 0, max_ot = 0, max_oc = 0;
+    for (const pb_panel &pn : p->panels) {
+        max_t = std::max(max_t, pn.tuples);
+        max_ot = std::max(max_ot, pn.over_tuples);
+        max_oc = std::max(max_oc, pn.c_hi - pn.c_lo);
+    }
+    // Workspace layout of the numeric phase (sized for the largest panel).
+    const size_t T = (size_t)max_t;
     const size_t nb = (size_t)p->hdr.nbins;
     size_t w = 0;
     p->ws_keys = w;
@@ -330,7 +410,7 @@ pb_status pb_spgemm_symbolic(pb_handle *h, const pb_csc *A, const pb_csr *B, pb_
     w += align256(8 * nb);
     p->ws_ctrl = w;
     w += 256;
-    const size_t OT = (size_t)p->hdr.over_tuples, OC = (size_t)p->hdr.over_chunks, NO = (size_t)p->hdr.n_oversize;
+    const size_t OT = (size_t)max_ot, OC = (size_t)max_oc, NO = (size_t)p->hdr.n_oversize;
     p->ws_skeys = w;
     w += align256(4 * OT);
     p->ws_svals = w;
@@ -351,7 +431,7 @@ pb_status pb_plan_query(const pb_plan *p, int64_t *flop, int64_t *c_cap, size_t 
     if (c_cap) *c_cap = p->hdr.flop;
     if (workspace_bytes) *workspace_bytes = p->ws_bytes;
     if (nbins) *nbins = p->hdr.nbins;
-    if (npanels) *npanels = 1;
+    if (npanels) *npanels = (int32_t)p->panels.size();
     return PB_OK;
 }
 
@@ -406,9 +486,15 @@ static pb_status fill_numeric(pb_handle *h, const pb_plan *p, const pb_csc *A, c
     return PB_OK;
 }
 
-static OversizeArgs oversize_args(const pb_plan *p, void *workspace) {
+static OversizeArgs oversize_args(const pb_plan *p, void *workspace, const pb_panel &pn) {
     char *w = static_cast<char *>(workspace);
     OversizeArgs o{};
+    o.o_lo = pn.o_lo;
+    o.o_hi = pn.o_hi;
+    o.c_lo = pn.c_lo;
+    o.c_hi = pn.c_hi;
+    o.tuple_base = pn.tuple_base;
+    o.over_base = pn.over_base;
     o.R = p->R;
     o.bin_row = p->bin_row;
     o.bin_off = p->bin_off;
@@ -460,15 +546,26 @@ pb_status pb_spgemm_numeric(pb_handle *h, const pb_plan *p, const pb_csc *A, con
         return PB_OK;
     }
     PB_CUDA(h, cudaMemcpyAsync(w + p->ws_cursor, p->bin_off, 8 * nb, cudaMemcpyDeviceToDevice, s));
-    PB_CUDA(h, cudaMemsetAsync(w + p->ws_status, 0, 8 * nb, s));
-    PB_CUDA(h, cudaMemsetAsync(w + p->ws_ctrl, 0, 256, s));
+    PB_CUDA(h, cudaMemsetAsync(w + p->ws_status, 0, 8 * nb, s));  // look-back words: all panels
     if (h->phase_on) PB_CUDA(h, cudaEventRecord(h->phase_ev[1], s));
-    PB_CUDA(h, launch_expand(a, s));
-    if (p->hdr.n_oversize > 0)
-        PB_CUDA(h, launch_oversize(oversize_args(p, workspace), p->over_passes, p->dtype, h->num_sms, s));
-    if (h->phase_on) PB_CUDA(h, cudaEventRecord(h->phase_ev[2], s));
-    PB_CUDA(h, launch_binsort(a, s));
-    if (h->phase_on) PB_CUDA(h, cudaEventRecord(h->phase_ev[3], s));
+    const bool single = p->panels.size() == 1;
+    for (const pb_panel &pn : p->panels) {
+        // panels run one after another: the look-back chain continues across them
+        a.bin_lo = pn.bin_lo;
+        a.bin_hi = pn.bin_hi;
+        a.tuple_base = pn.tuple_base;
+        a.over_base = pn.over_base;
+        PB_CUDA(h, cudaMemsetAsync(w + p->ws_ctrl, 0, 256, s));
+        PB_CUDA(h, launch_expand(a, s));
+        if (pn.o_hi > pn.o_lo)
+            PB_CUDA(h, launch_oversize(oversize_args(p, workspace, pn), p->over_passes, p->dtype, h->num_sms, s));
+        if (h->phase_on && single) PB_CUDA(h, cudaEventRecord(h->phase_ev[2], s));
+        PB_CUDA(h, launch_binsort(a, s));
+    }
+    if (h->phase_on) {
+        if (!single) PB_CUDA(h, cudaEventRecord(h->phase_ev[2], s));
+        PB_CUDA(h, cudaEventRecord(h->phase_ev[3], s));
+    }
     return PB_OK;
 }
 
@@ -495,6 +592,11 @@ pb_status pb_debug_expand(pb_handle *h, const pb_plan *p, const pb_csc *A, const
     if (st != PB_OK) return st;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream_);
     char *w = static_cast<char *>(workspace);
+    const pb_panel &pn = p->panels.front();  // the first panel's tuples
+    a.bin_lo = pn.bin_lo;
+    a.bin_hi = pn.bin_hi;
+    a.tuple_base = pn.tuple_base;
+    a.over_base = pn.over_base;
     PB_CUDA(h, cudaMemcpyAsync(w + p->ws_cursor, p->bin_off, 8 * (size_t)p->hdr.nbins, cudaMemcpyDeviceToDevice, s));
     PB_CUDA(h, launch_expand(a, s));
     return PB_OK;

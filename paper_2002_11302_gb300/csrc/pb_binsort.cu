@@ -247,8 +247,8 @@ __device__ void stream_oversize_bin(const NumericArgs &p, int64_t b, int32_t row
     const int tid = threadIdx.x;
     const int64_t o = p.over_scan[b];
     const bool in_scratch = (p.over_passes & 1) != 0;
-    const uint32_t *k = in_scratch ? p.skeys + p.over_tuple_off[o] : p.keys + off;
-    const TV *v = in_scratch ? static_cast<const TV *>(p.svals) + p.over_tuple_off[o]
+    const uint32_t *k = in_scratch ? p.skeys + (p.over_tuple_off[o] - p.over_base) : p.keys + off;
+    const TV *v = in_scratch ? static_cast<const TV *>(p.svals) + (p.over_tuple_off[o] - p.over_base)
                              : static_cast<const TV *>(p.vals) + off;
     OV *valC = static_cast<OV *>(p.valC);
     if (tid < 32) publish_and_check(p, b, p.over_u[o], prefix, okp);
@@ -297,13 +297,13 @@ __global__ void __launch_bounds__(THREADS, (THREADS <= 256 ? 4 : (THREADS <= 512
     uint32_t phase = 0;
 
     while (true) {
-        if (tid == 0) sm.bin = (int64_t)atomicAdd(p.ticket, 1u);
+        if (tid == 0) sm.bin = p.bin_lo + (int64_t)atomicAdd(p.ticket, 1u);
         fence_proxy_async_smem();  // earlier generic smem accesses before the next bulk copy
         __syncthreads();
         const int64_t b = sm.bin;
-        if (b >= p.nbins) break;
+        if (b >= p.bin_hi) break;
         const int32_t row0 = p.bin_row[b], row1 = p.bin_row[b + 1];
-        const int64_t off = p.bin_off[b];
+        const int64_t off = p.bin_off[b] - p.tuple_base;  // the buffer holds this panel's tuples
         const int64_t Nfull = p.R[row1] - p.R[row0];
         if (Nfull > CAP) {
             stream_oversize_bin<THREADS, TV, OV>(p, b, row0, row1, off, Nfull, colmask, sm.scratch, &sm.prefix,
@@ -537,7 +537,7 @@ cudaError_t run_binsort(const NumericArgs &a, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
     int64_t grid = (int64_t)a.num_sms * per_sm;
-    if (grid > a.nbins) grid = a.nbins;
+    if (grid > a.bin_hi - a.bin_lo) grid = a.bin_hi - a.bin_lo;
     if (grid < 1) return cudaSuccess;
     kern<<<(unsigned)grid, THREADS, smem, s>>>(a);
     count_launches(1);
@@ -557,7 +557,7 @@ cudaError_t dispatch_cap(const NumericArgs &a, cudaStream_t s) {
 }  // namespace
 
 cudaError_t launch_binsort(const NumericArgs &a, cudaStream_t s) {
-    if (a.nbins <= 0) return cudaSuccess;
+    if (a.bin_hi <= a.bin_lo) return cudaSuccess;
     switch (a.dtype) {
         case PB_F64: return dispatch_cap<double, double>(a, s);
         case PB_F32: return dispatch_cap<float, float>(a, s);

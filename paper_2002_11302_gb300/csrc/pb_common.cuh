@@ -79,8 +79,12 @@ struct OversizeArgs {
     void *vals;
     uint32_t *skeys;
     void *svals;
-    uint32_t *hist;   // [over_chunks * 256]
+    uint32_t *hist;   // [(c_hi - c_lo) * 256]
     int64_t *over_u;  // [n_over] merged entries of each oversize bin
+    // the panel being processed: oversize bins [o_lo, o_hi), their work items
+    // [c_lo, c_hi); tuple offsets are relative to tuple_base (main buffer) and
+    // over_base (scratch)
+    int64_t o_lo, o_hi, c_lo, c_hi, tuple_base, over_base;
 };
 
 template <class T>
@@ -231,6 +235,9 @@ struct NumericArgs {
     int64_t flop, nbins, nchunks, chunk;
     int32_t colbits;
     int32_t capacity;
+    // the panel being processed: bins [bin_lo, bin_hi); the tuple buffer holds
+    // tuples [tuple_base, tuple_base + panel size) of the whole product
+    int64_t bin_lo, bin_hi, tuple_base, over_base;
     // workspace
     uint32_t *keys;
     void *vals;

@@ -62,9 +62,12 @@ __device__ inline Batch<IV> load_batch(const NumericArgs &p, const IV *__restric
     if (valid) {
         const int32_t k = p.acol[e];
         x.info = p.ainfo[e];
-        x.av = valA[e];
-        x.b0 = p.rowptrB[k];
-        x.lb = p.rowptrB[k + 1] - x.b0;
+        const int64_t bin = (int64_t)(x.info >> 32);
+        if (bin >= p.bin_lo && bin < p.bin_hi) {  // the entry's row belongs to this panel
+            x.av = valA[e];
+            x.b0 = p.rowptrB[k];
+            x.lb = p.rowptrB[k + 1] - x.b0;
+        }
     }
     return x;
 }
@@ -77,8 +80,10 @@ __global__ void __launch_bounds__(256) k_expand(const NumericArgs p) {
     const IV *__restrict__ valA = static_cast<const IV *>(p.valA);
     const IV *__restrict__ valB = static_cast<const IV *>(p.valB);
     const int32_t *__restrict__ colidxB = p.colidxB;
-    uint32_t *__restrict__ keys = p.keys;
-    TV *__restrict__ vals = static_cast<TV *>(p.vals);
+    // reserved positions are absolute tuple indices of the whole product; the
+    // buffer holds this panel's tuples from tuple_base on
+    uint32_t *__restrict__ keys = p.keys - p.tuple_base;
+    TV *__restrict__ vals = static_cast<TV *>(p.vals) - p.tuple_base;
 
     for (int64_t c = gwarp; c < p.nchunks; c += nwarps) {
         const int32_t e_begin = p.chunk_e[c], e_end = p.chunk_e[c + 1];

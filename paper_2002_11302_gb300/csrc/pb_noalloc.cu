@@ -207,6 +207,10 @@ extern "C" pb_status pb_spgemm_noalloc(const pb_csc *A, const pb_csr *B, pb_dtyp
     na.over_u = over_u;
     na.svals = svals;
     na.over_passes = over_passes;
+    na.bin_lo = 0;  // one panel: the whole product
+    na.bin_hi = hdr.nbins;
+    na.tuple_base = 0;
+    na.over_base = 0;
 
     if (m == 0) {
         if (C->rowptr64) PB_NA_CUDA(cudaMemsetAsync(C->rowptr64, 0, 8, s));
@@ -237,6 +241,12 @@ extern "C" pb_status pb_spgemm_noalloc(const pb_csc *A, const pb_csr *B, pb_dtyp
         o.svals = svals;
         o.hist = hist;
         o.over_u = over_u;
+        o.o_lo = 0;
+        o.o_hi = hdr.n_oversize;
+        o.c_lo = 0;
+        o.c_hi = hdr.over_chunks;
+        o.tuple_base = 0;
+        o.over_base = 0;
         PB_NA_CUDA(launch_oversize(o, over_passes, dtype, na.num_sms, s));
     }
     PB_NA_CUDA(launch_binsort(na, s));

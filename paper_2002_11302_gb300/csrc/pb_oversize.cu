@@ -41,10 +41,10 @@ __device__ inline ChunkRef chunk_ref(const OversizeArgs &a, int64_t c) {
 template <class TV>
 __device__ inline void pass_buffers(const OversizeArgs &a, int pass, const ChunkRef &r, const uint32_t *&sk,
                                     const TV *&sv, uint32_t *&dk, TV *&dv) {
-    uint32_t *mk = a.keys + a.bin_off[r.bin];
-    TV *mv = static_cast<TV *>(a.vals) + a.bin_off[r.bin];
-    uint32_t *xk = a.skeys + a.over_tuple_off[r.o];
-    TV *xv = static_cast<TV *>(a.svals) + a.over_tuple_off[r.o];
+    uint32_t *mk = a.keys + (a.bin_off[r.bin] - a.tuple_base);
+    TV *mv = static_cast<TV *>(a.vals) + (a.bin_off[r.bin] - a.tuple_base);
+    uint32_t *xk = a.skeys + (a.over_tuple_off[r.o] - a.over_base);
+    TV *xv = static_cast<TV *>(a.svals) + (a.over_tuple_off[r.o] - a.over_base);
     if ((pass & 1) == 0) {
         sk = mk; sv = mv; dk = xk; dv = xv;
     } else {
@@ -56,7 +56,7 @@ template <class TV>
 __global__ void __launch_bounds__(OT) k_over_hist(const OversizeArgs a, int pass) {
     __shared__ uint32_t h[256];
     const int shift = 8 * pass;
-    for (int64_t c = blockIdx.x; c < a.over_chunks; c += gridDim.x) {
+    for (int64_t c = a.c_lo + blockIdx.x; c < a.c_hi; c += gridDim.x) {
         const ChunkRef r = chunk_ref(a, c);
         const uint32_t *sk;
         const TV *sv;
@@ -67,7 +67,7 @@ __global__ void __launch_bounds__(OT) k_over_hist(const OversizeArgs a, int pass
         __syncthreads();
         for (int64_t q = threadIdx.x; q < r.len; q += OT) atomicAdd(&h[(sk[r.start + q] >> shift) & 255u], 1u);
         __syncthreads();
-        for (int i = threadIdx.x; i < 256; i += OT) a.hist[c * 256 + i] = h[i];
+        for (int i = threadIdx.x; i < 256; i += OT) a.hist[(c - a.c_lo) * 256 + i] = h[i];
         __syncthreads();
     }
 }
@@ -77,8 +77,8 @@ __global__ void __launch_bounds__(OT) k_over_hist(const OversizeArgs a, int pass
 __global__ void __launch_bounds__(256) k_over_offsets(const OversizeArgs a) {
     __shared__ int64_t scratch[40];
     const int d = threadIdx.x;  // one digit value per thread
-    for (int64_t o = blockIdx.x; o < a.n_over; o += gridDim.x) {
-        const int64_t c0 = a.over_chunk_off[o], c1 = a.over_chunk_off[o + 1];
+    for (int64_t o = a.o_lo + blockIdx.x; o < a.o_hi; o += gridDim.x) {
+        const int64_t c0 = a.over_chunk_off[o] - a.c_lo, c1 = a.over_chunk_off[o + 1] - a.c_lo;
         uint32_t run = 0;
         for (int64_t c = c0; c < c1; ++c) {
             const uint32_t v = a.hist[c * 256 + d];
@@ -97,7 +97,7 @@ __global__ void __launch_bounds__(OT) k_over_scatter(const OversizeArgs a, int p
     __shared__ uint32_t wc[256 * ONW];  // per (digit, warp) counts, then in-chunk offsets
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int shift = 8 * pass;
-    for (int64_t c = blockIdx.x; c < a.over_chunks; c += gridDim.x) {
+    for (int64_t c = a.c_lo + blockIdx.x; c < a.c_hi; c += gridDim.x) {
         const ChunkRef r = chunk_ref(a, c);
         const uint32_t *sk;
         const TV *sv;
@@ -149,7 +149,7 @@ __global__ void __launch_bounds__(OT) k_over_scatter(const OversizeArgs a, int p
             const int64_t q = warp * OWS + j * 32 + lane;
             if (q < r.len) {
                 const uint32_t dg = (kk[j] >> shift) & 255u;
-                const int64_t pos = (int64_t)a.hist[c * 256 + dg] + wc[dg * ONW + warp] + lr[j];
+                const int64_t pos = (int64_t)a.hist[(c - a.c_lo) * 256 + dg] + wc[dg * ONW + warp] + lr[j];
                 dk[pos] = kk[j];
                 dv[pos] = vv[j];
             }
@@ -161,9 +161,10 @@ __global__ void __launch_bounds__(OT) k_over_scatter(const OversizeArgs a, int p
 // Number of merged entries of each oversize bin = number of run heads.
 __global__ void __launch_bounds__(OT) k_over_heads(const OversizeArgs a, int passes) {
     __shared__ int64_t scratch[40];
-    for (int64_t c = blockIdx.x; c < a.over_chunks; c += gridDim.x) {
+    for (int64_t c = a.c_lo + blockIdx.x; c < a.c_hi; c += gridDim.x) {
         const ChunkRef r = chunk_ref(a, c);
-        const uint32_t *k = (passes & 1) ? a.skeys + a.over_tuple_off[r.o] : a.keys + a.bin_off[r.bin];
+        const uint32_t *k = (passes & 1) ? a.skeys + (a.over_tuple_off[r.o] - a.over_base)
+                                         : a.keys + (a.bin_off[r.bin] - a.tuple_base);
         int64_t heads = 0;
         for (int64_t q = threadIdx.x; q < r.len; q += OT) {
             const int64_t p = r.start + q;
@@ -178,9 +179,10 @@ __global__ void __launch_bounds__(OT) k_over_heads(const OversizeArgs a, int pas
 template <class TV>
 cudaError_t run_oversize(const OversizeArgs &a, int passes, int num_sms, cudaStream_t s) {
     const int64_t g4 = (int64_t)num_sms * 4, g8 = (int64_t)num_sms * 8;
-    const unsigned grid = (unsigned)(a.over_chunks < g4 ? a.over_chunks : g4);
-    const unsigned ogrid = (unsigned)(a.n_over < g8 ? a.n_over : g8);
-    cudaError_t e = cudaMemsetAsync(a.over_u, 0, 8 * (size_t)a.n_over, s);
+    const int64_t nc = a.c_hi - a.c_lo, no = a.o_hi - a.o_lo;
+    const unsigned grid = (unsigned)(nc < g4 ? nc : g4);
+    const unsigned ogrid = (unsigned)(no < g8 ? no : g8);
+    cudaError_t e = cudaMemsetAsync(a.over_u + a.o_lo, 0, 8 * (size_t)no, s);
     if (e != cudaSuccess) return e;
     for (int pass = 0; pass < passes; ++pass) {
         k_over_hist<TV><<<grid, OT, 0, s>>>(a, pass);
@@ -196,7 +198,7 @@ cudaError_t run_oversize(const OversizeArgs &a, int passes, int num_sms, cudaStr
 }  // namespace
 
 cudaError_t launch_oversize(const OversizeArgs &a, int passes, int dtype, int num_sms, cudaStream_t s) {
-    if (a.n_over <= 0) return cudaSuccess;
+    if (a.o_hi <= a.o_lo) return cudaSuccess;
     if (dtype == PB_F64) return run_oversize<double>(a, passes, num_sms, s);
     return run_oversize<float>(a, passes, num_sms, s);
 }

@@ -241,3 +241,47 @@ def test_er_full_size_sampled_rows(pb):
     assert_rows_match(C, oracle.spgemm(A, B, rows), EPS["f64"])
     nnz = int(C.rowptr[-1].item())
     assert nnz <= n * d * d
+
+
+@pytest.mark.parametrize("budget_tuples", [20000, 60000])
+def test_row_panels_match_oracle(pb, budget_tuples):
+    """Products whose tuples exceed the workspace budget run in several row panels."""
+    A, B = synth.er(30000, 6, seed=81, shuffle_within=True)
+    Ad, Bd = pb.csc_to_device(A), pb.csr_to_device(B)
+    cfg = pb.make_config(max_tuple_bytes=budget_tuples * 12)
+    plan = pb.symbolic(Ad, Bd, config=cfg)
+    assert plan.npanels > 1
+    C = pb.alloc_output(plan)
+    pb.numeric(plan, Ad, Bd, C, plan.workspace())
+    assert plan.status() == 0
+    n = int(C.rowptr[-1].item())
+    C = pb.CsrMatrix(C.nrows, C.ncols, C.rowptr, C.colidx[:n], C.val[:n])
+    assert_matches(C, oracle.spgemm(A, B), EPS["f64"])
+
+
+def test_row_panels_with_oversize_rows(pb):
+    A, B = synth.rmat(12, 8, seed=82)
+    cfg = pb.make_config(max_tuple_bytes=400000 * 12)
+    Ad, Bd = pb.csc_to_device(A), pb.csr_to_device(B)
+    plan = pb.symbolic(Ad, Bd, config=cfg)
+    assert plan.npanels > 1
+    C = pb.alloc_output(plan)
+    pb.numeric(plan, Ad, Bd, C, plan.workspace())
+    assert plan.status() == 0
+    n = int(C.rowptr[-1].item())
+    C = pb.CsrMatrix(C.nrows, C.ncols, C.rowptr, C.colidx[:n], C.val[:n])
+    assert_matches(C, oracle.spgemm(A, B), EPS["f64"])
+
+
+def test_counting_run_gives_exact_nnz(pb):
+    A, B = synth.rmat(11, 8, seed=83)
+    Ad, Bd = pb.csc_to_device(A), pb.csr_to_device(B)
+    plan = pb.symbolic(Ad, Bd)
+    nnz = torch.zeros(1, dtype=torch.int64, device="cuda")
+    empty = pb.CsrMatrix(plan.m, plan.n, torch.empty(0, dtype=torch.int64, device="cuda"),
+                         torch.empty(0, dtype=torch.int32, device="cuda"),
+                         torch.empty(0, dtype=torch.float64, device="cuda"))
+    pb.numeric_count(plan, Ad, Bd, plan.workspace(), nnz)
+    assert plan.status() == 0
+    assert int(nnz.item()) == oracle.spgemm(A, B).nnz
+    del empty
