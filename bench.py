@@ -38,8 +38,12 @@ METRIC = "SpGEMM GFLOPS and HBM GB/s as % of β·AI roofline; served p50/p99 lat
 WORKLOADS = {
     "er21": dict(kind="er", n=1 << 21, d=8, seed=1, dtype="f64",
                  desc="ER C=A*A, n=2^21, d=8 per column, FP64 values U(-1,1), int32 indices"),
+    "rmat20": dict(kind="rmat", scale=20, ef=16, seed=2, dtype="f64", budget=64 << 30, exact=True,
+                   desc="R-MAT C=A*A, scale 20, edge factor 16, (0.57,0.19,0.19,0.05), dedup, FP64, row panels"),
     "er22": dict(kind="er", n=1 << 22, d=8, seed=4, dtype="f64",
                  desc="ER C=A*A, n=2^22, d=8 per column, FP64 values U(-1,1), int32 indices"),
+    "er22f32t": dict(kind="er", n=1 << 22, d=8, seed=4, dtype="f64_f32tuple",
+                     desc="ER C=A*A, n=2^22, d=8, FP64 values, FP32 tuples merged in FP64, int32 indices"),
     "er19": dict(kind="er", n=1 << 19, d=8, seed=7, dtype="f64",
                  desc="ER C=A*A, n=2^19, d=8 per column, FP64 values U(-1,1), int32 indices"),
     "er12": dict(kind="er", n=4096, d=4, seed=0, dtype="f64",
@@ -49,6 +53,8 @@ WORKLOADS = {
 
 def make_inputs(w):
     import synth
+    if w["kind"] == "rmat":
+        return synth.rmat(w["scale"], w["ef"], seed=w["seed"])
     return synth.er(w["n"], w["d"], seed=w["seed"])
 
 
@@ -129,14 +135,34 @@ class ClockSampler:
                 "samples": len(sms)}
 
 
-def cpu_oracle_run(A, B, repeats: int):
+def oracle_rows_for_budget(A, B, budget_s: float):
+    """Leading rows whose oracle product takes about budget_s seconds (cost model
+    t(rows) = t_fixed + c * flop(rows), from a 1-row call and a 1/16 sample)."""
     import oracle
+    rf = oracle.row_flop(A, B)
+    t0 = time.perf_counter()
+    oracle.spgemm(A, B, np.zeros(1, np.int64))
+    t_fixed = time.perf_counter() - t0
+    probe = max(2, A.nrows // 16)
+    t0 = time.perf_counter()
+    oracle.spgemm(A, B, np.arange(probe, dtype=np.int64))
+    c = max(time.perf_counter() - t0 - t_fixed, 1e-9) / max(int(rf[:probe].sum()), 1)
+    cum = np.cumsum(rf)
+    want = max((budget_s - t_fixed) / c, 1.0)
+    nrows = int(min(A.nrows, max(np.searchsorted(cum, want) + 1, A.nrows // 256, 1)))
+    return np.arange(nrows, dtype=np.int64), int(rf[:nrows].sum())
+
+
+def cpu_oracle_run(A, B, repeats: int, budget_s: float = 8.0):
+    """Median time of the oracle on a bounded leading-row sample; returns (seconds, cores, flop, nrows)."""
+    import oracle
+    rows, flop = oracle_rows_for_budget(A, B, budget_s)
     ts = []
     for _ in range(repeats):
         t0 = time.perf_counter()
-        oracle.spgemm(A, B)
+        oracle.spgemm(A, B, rows if rows.shape[0] < A.nrows else None)
         ts.append(time.perf_counter() - t0)
-    return statistics.median(ts), oracle.threads()
+    return statistics.median(ts), oracle.threads(), flop, rows.shape[0]
 
 
 def run_reference(args, w):
@@ -148,19 +174,8 @@ def run_reference(args, w):
     A, B = make_inputs(w)
     # Each step is a bounded sample: a contiguous block of rows sized so the
     # whole run (warm-up + timed steps) stays near two minutes of CPU time.
-    # Cost model t(rows) = t_fixed + c * rows from a 1-row call and a 1/16 sample.
-    t0 = time.perf_counter()
-    oracle.spgemm(A, B, np.zeros(1, np.int64))
-    t_fixed = time.perf_counter() - t0
-    probe = max(2, A.nrows // 16)
-    t0 = time.perf_counter()
-    oracle.spgemm(A, B, np.arange(probe, dtype=np.int64))
-    c = max(time.perf_counter() - t0 - t_fixed, 1e-9) / probe
-    budget = 120.0 / (args.steps + args.warmup)
-    nrows = int(min(A.nrows, max(A.nrows // 256, (budget - t_fixed) / c, 1)))
-    rows = np.arange(nrows, dtype=np.int64)
-    rowflop = oracle.row_flop(A, B)
-    flop = int(rowflop[:nrows].sum())
+    rows, flop = oracle_rows_for_budget(A, B, 120.0 / (args.steps + args.warmup))
+    nrows = rows.shape[0]
     for _ in range(args.warmup):
         oracle.spgemm(A, B, rows)
     t0 = time.perf_counter()
@@ -198,18 +213,25 @@ def run_ours(args, w):
     Ad, Bd = binding.csc_to_device(A), binding.csr_to_device(B)
     handle = binding.Handle()
     stream = torch.cuda.current_stream()
-    cfg = binding.make_config(bin_capacity=args.capacity, expand_chunk=args.chunk)
-    plan = binding.symbolic(Ad, Bd, config=cfg, handle=handle)
+    cfg = binding.make_config(bin_capacity=args.capacity, expand_chunk=args.chunk,
+                              max_tuple_bytes=w.get("budget", 0))
+    dt = {"f64": binding.PB_F64, "f64_f32tuple": binding.PB_F64_F32TUPLE}[w["dtype"]]
+    plan = binding.symbolic(Ad, Bd, dtype=dt, config=cfg, handle=handle)
     flop = plan.flop
-    C = binding.alloc_output(plan, rowptr64=True)
     ws = plan.workspace()
+    cap = None
+    if w.get("exact"):  # size C by a counting run (a flop-sized C would not fit)
+        cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+        binding.numeric_count(plan, Ad, Bd, ws, cnt)
+        cap = int(cnt.item())
+    C = binding.alloc_output(plan, rowptr64=True, cap=cap)
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
     binding.set_phase_events(handle, ev)
 
     def step(record=None):
         if record is not None:
             record[0].record(stream)
-        p = binding.symbolic(Ad, Bd, config=cfg, handle=handle)
+        p = binding.symbolic(Ad, Bd, dtype=dt, config=cfg, handle=handle)
         if record is not None:
             record[1].record(stream)
         binding.numeric(p, Ad, Bd, C, ws)
@@ -260,8 +282,9 @@ def run_ours(args, w):
     value = 2.0 * flop * args.steps * world / (total_ms / 1e3) / 1e9
 
     # roofline of the dominant kernel (algorithmic bytes per launch / event-timed duration)
-    by = model.bytes_alg(A.nrows, A.ncols, A.nnz, B.nnz, flop, nnz_c, val_in=8, tuple_bytes=12, val_out=8,
-                         rowptr_out=8)
+    tuple_bytes = 12 if dt == binding.PB_F64 else 8
+    by = model.bytes_alg(A.nrows, A.ncols, A.nnz, B.nnz, flop, nnz_c, val_in=8, tuple_bytes=tuple_bytes,
+                         val_out=8, rowptr_out=8)
     hbm, peak_kind = measured_peaks()
     kern = {"expand": (by.expand, phase_ms["expand"] / args.steps, "k_expand", "pb_expand.cu"),
             "sort_compress": (by.sort + by.compress, phase_ms["sort_compress"] / args.steps, "k_binsort",
@@ -276,10 +299,11 @@ def run_ours(args, w):
     line = {
         "metric": METRIC, "value": value, "unit": "GFLOPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": w["desc"], "n": w["n"], "d": w["d"], "flop": flop, "nnz_c": nnz_c,
+        "vs_baseline": None, "dtype": "f64" if dt == binding.PB_F64 else "f64 (f32 tuples)", "data": "synthetic",
+        "config": {"workload": w["desc"], "n": A.nrows, "nnz_a": A.nnz, "flop": flop, "nnz_c": nnz_c,
+                   "npanels": plan.npanels, "tuple_bytes": tuple_bytes,
                    "cf": flop / max(nnz_c, 1), "nbins": plan.nbins, "bin_capacity": args.capacity or 4096,
-                   "l2": "no flush: inputs (0.4 GB) and tuples (1.6 GB) exceed the 129 MB L2",
+                   "l2": "no flush: the inputs and the tuple buffer each exceed the 129 MB L2",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "peak_kind": peak_kind,
@@ -293,12 +317,13 @@ def run_ours(args, w):
         "clocks": clocks,
     }
 
-    if not args.no_e2e:
+    if not args.no_e2e and not w.get("exact"):
         line["e2e"] = run_e2e(args, A, B, handle, torch, binding)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        t, cores = cpu_oracle_run(A, B, repeats=3)
-        line["cpu_baseline"] = {"value": 2.0 * flop / t / 1e9, "unit": "GFLOPS", "cores": cores, "kind": "oracle",
-                                "sample": "the full product (all rows), median of 3 runs"}
+        t, cores, sflop, srows = cpu_oracle_run(A, B, repeats=3)
+        line["cpu_baseline"] = {"value": 2.0 * sflop / t / 1e9, "unit": "GFLOPS", "cores": cores, "kind": "oracle",
+                                "sample": f"rows 0..{srows - 1} of {A.nrows} ({sflop} of {flop} multiplications), "
+                                          f"median of 3 runs"}
     binding.set_phase_events(handle, None)
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -357,6 +357,27 @@ def alloc_output(plan: Plan, rowptr64: bool = True, cap: Optional[int] = None) -
                      torch.empty(max(cap, 1), dtype=_OUT_DTYPE[plan.dtype], device=dev))
 
 
+def spgemm_exact(A: CscMatrix, B: CsrMatrix, dtype: int = PB_F64, config: Optional[_Config] = None,
+                 rowptr64: bool = True, handle: Optional[Handle] = None):
+    """C = A * B with C allocated at exactly nnz(C) (a counting run first); returns (C, plan).
+
+    For products whose flop-sized output would not fit in device memory.
+    """
+    plan = symbolic(A, B, dtype, config, handle)
+    ws = plan.workspace()
+    nnz = torch.zeros(1, dtype=torch.int64, device="cuda")
+    numeric_count(plan, A, B, ws, nnz)
+    if plan.status() != 0:
+        raise PBError(plan.status(), "device-side error in the counting run")
+    C = alloc_output(plan, rowptr64, cap=int(nnz.item()))
+    numeric(plan, A, B, C, ws)
+    st = plan.status()
+    if st != 0:
+        raise PBError(st, "device-side error in the numeric phase")
+    k = int(nnz.item())
+    return CsrMatrix(C.nrows, C.ncols, C.rowptr, C.colidx[:k], C.val[:k]), plan
+
+
 def spgemm(A: CscMatrix, B: CsrMatrix, dtype: int = PB_F64, config: Optional[_Config] = None,
            rowptr64: bool = True, handle: Optional[Handle] = None) -> CsrMatrix:
     """C = A * B on the current stream; returns C trimmed to nnz(C).  Synchronises."""

@@ -285,3 +285,36 @@ def test_counting_run_gives_exact_nnz(pb):
     assert plan.status() == 0
     assert int(nnz.item()) == oracle.spgemm(A, B).nnz
     del empty
+
+
+def _rows_from_device(C, rows):
+    """Row segments of a device CSR for the listed rows (copies only those)."""
+    rp = C.rowptr.cpu().numpy().astype(np.int64)
+    out = []
+    for i in rows:
+        a, b = int(rp[i]), int(rp[i + 1])
+        out.append((C.colidx[a:b].cpu().numpy(), C.val[a:b].double().cpu().numpy()))
+    return rp, out
+
+
+@pytest.mark.slow
+def test_rmat_scale20_full_size_sampled_rows(pb):
+    """R-MAT scale 20, edge factor 16, (0.57, 0.19, 0.19, 0.05), C = A*A: 2.1e10 tuples,
+    nnz(C) above 2^31, hub rows far above a bin's capacity.  Runs in row panels with
+    C sized by a counting run; sampled rows (the heaviest included) match the oracle."""
+    A, B = synth.rmat(20, 16, seed=2)
+    Ad, Bd = pb.csc_to_device(A), pb.csr_to_device(B)
+    cfg = pb.make_config(max_tuple_bytes=64 << 30)
+    C, plan = pb.spgemm_exact(Ad, Bd, config=cfg)
+    assert plan.npanels > 1
+    assert plan.flop == oracle.flop(A, B)
+    rf = oracle.row_flop(A, B)
+    rng = np.random.default_rng(5)
+    rows = np.unique(np.concatenate([np.argsort(rf)[-20:], rng.choice(A.nrows, 200, replace=False), [0, A.nrows - 1]]))
+    ref = oracle.spgemm(A, B, rows)
+    rp, segs = _rows_from_device(C, rows)
+    assert rp[0] == 0 and np.all(np.diff(rp) >= 0) and rp[-1] == C.nnz
+    for t, (cols, vals) in enumerate(segs):
+        ra, rb = ref.rowptr[t], ref.rowptr[t + 1]
+        assert np.array_equal(cols, ref.colidx[ra:rb]), f"row {rows[t]}: columns differ"
+        assert np.all(np.abs(vals - ref.val[ra:rb]) <= 64 * EPS["f64"] * ref.absval[ra:rb])
