@@ -227,6 +227,7 @@ pb_status pb_spgemm_symbolic(pb_handle *h, const pb_csc *A, const pb_csr *B, pb_
     const size_t oH = take(sizeof(PlanHeader)), oT = take(8 * scan_tmp_elems(scan_n)), oE = take(64);
     const size_t oOs = take(8 * (m + 1)), oOb = take(8 * (m + 1)), oOc = take(8 * (m + 1)), oOt = take(8 * (m + 1));
     const size_t oAi = take(8 * (p->nnzA > 0 ? p->nnzA : 1)), oAc = take(4 * (p->nnzA > 0 ? p->nnzA : 1));
+    const size_t oLc = take(4 * (k > 0 ? k : 1) + 256);
     p->arena_bytes = off;
     p->arena = h->alloc(p->arena_bytes, stream_, h->ctx);
     if (!p->arena) {
@@ -273,6 +274,9 @@ pb_status pb_spgemm_symbolic(pb_handle *h, const pb_csc *A, const pb_csr *B, pb_
     a.flags = p->flags;
     a.rowinfo = p->rowinfo;
     a.ainfo = p->ainfo;
+    a.acol = p->acol;
+    a.long_cols = reinterpret_cast<int32_t *>(base + oLc);
+    a.n_long = reinterpret_cast<uint32_t *>(base + oLc + 4 * (k > 0 ? k : 1));
     a.nnzA = p->nnzA;
     a.bin_row = p->bin_row;
     a.bin_off = p->bin_off;
@@ -299,6 +303,15 @@ pb_status pb_spgemm_symbolic(pb_handle *h, const pb_csc *A, const pb_csr *B, pb_
         fail(h, PB_ERR_UNSUPPORTED, "a single row produces 2^31 or more tuples");
         return bail(PB_ERR_UNSUPPORTED);
     }
+    if (p->hdr.max_bin_count > (unsigned long long)p->capacity) {
+        // some rows exceed a bin: build their lists (a second, rarer readback)
+        if ((e = launch_symbolic_oversize(a, p->scan_tmp, s)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(&p->hdr, p->dhdr, sizeof(PlanHeader), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+            (e = cudaStreamSynchronize(s)) != cudaSuccess) {
+            cuda_fail(h, e, "oversize lists");
+            return bail(PB_ERR_CUDA);
+        }
+    }
     // Oversize bins: work-item map for their global-memory radix sort.
     if (p->hdr.n_oversize > 0) {
         p->over_passes = (p->colbits + 7) / 8;
@@ -323,8 +336,7 @@ pb_status pb_spgemm_symbolic(pb_handle *h, const pb_csc *A, const pb_csr *B, pb_
         return bail(PB_ERR_OOM);
     }
     p->chunk_e = static_cast<int32_t *>(p->chunk_mem);
-    if ((e = launch_chunk_table(p->F, A->colptr, B->rowptr, p->k, p->nnzA, p->nchunks, p->chunk, p->chunk_e, p->acol,
-                                s)) != cudaSuccess) {
+    if ((e = launch_chunk_table(a, p->nchunks, p->chunk, p->chunk_e, s)) != cudaSuccess) {
         cuda_fail(h, e, "chunk table");
         return bail(PB_ERR_CUDA);
     }

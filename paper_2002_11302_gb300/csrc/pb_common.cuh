@@ -55,6 +55,9 @@ struct SymbolicArgs {
     int64_t *flags;      // [m+1] scratch: bin-start flags, then their exclusive scan
     uint64_t *rowinfo;   // [m]   (bin << 32) | (local_row << colbits)
     uint64_t *ainfo;     // [nnzA] rowinfo of each A entry's row
+    int32_t *acol;       // [nnzA] column of each A entry
+    int32_t *long_cols;  // [k] scratch: columns with many entries
+    uint32_t *n_long;    // [1] scratch counter
     int64_t nnzA;
     int32_t *bin_row;    // [m+2]
     int64_t *bin_off;    // [m+2]
@@ -213,8 +216,9 @@ void count_launches(int64_t n);
 
 // Kernel launchers implemented in the other translation units.
 cudaError_t launch_symbolic(const SymbolicArgs &a, int64_t *scan_tmp, cudaStream_t s);
-cudaError_t launch_chunk_table(const int64_t *F, const int32_t *colptrA, const int32_t *rowptrB, int32_t k,
-                               int64_t nnzA, int64_t nchunks, int64_t chunk, int32_t *chunk_e, int32_t *acol,
+cudaError_t launch_symbolic_oversize(const SymbolicArgs &a, int64_t *scan_tmp, cudaStream_t s);
+// Per-A-entry pass after the sizes are known: ainfo and the expand work items.
+cudaError_t launch_chunk_table(const SymbolicArgs &a, int64_t nchunks, int64_t chunk, int32_t *chunk_e,
                                cudaStream_t s);
 cudaError_t launch_over_chunk_map(const int64_t *over_chunk_off, int64_t n_over, int32_t *over_chunk_bin,
                                   cudaStream_t s);

@@ -108,6 +108,7 @@ extern "C" pb_status pb_spgemm_noalloc(const pb_csc *A, const pb_csr *B, pb_dtyp
 
     // ---- plan arrays (same layout as a plan made by pb_spgemm_symbolic) -----------
     SymbolicArgs a{};
+    int32_t *acol = nullptr;
     int64_t *scan_tmp = nullptr;
     uint32_t *err = nullptr;
     const size_t m1 = (size_t)m + 1, m2 = (size_t)m + 2;
@@ -118,8 +119,8 @@ extern "C" pb_status pb_spgemm_noalloc(const pb_csc *A, const pb_csr *B, pb_dtyp
               cv.take(scan_tmp, 8 * (size_t)scan_tmp_elems((int64_t)scan_n)) && cv.take(err, 64) &&
               cv.take(a.over_scan, 8 * m1) && cv.take(a.over_bin, 8 * m1) && cv.take(a.over_chunk_off, 8 * m1) &&
               cv.take(a.over_tuple_off, 8 * m1) && cv.take(a.ainfo, 8 * (nnzA > 0 ? (size_t)nnzA : 1));
-    int32_t *acol = nullptr;
-    ok = ok && cv.take(acol, 4 * (nnzA > 0 ? (size_t)nnzA : 1));
+    ok = ok && cv.take(acol, 4 * (nnzA > 0 ? (size_t)nnzA : 1)) && cv.take(a.long_cols, 4 * (k > 0 ? (size_t)k : 1)) &&
+         cv.take(a.n_long, 4);
     if (!ok) return PB_ERR_WORKSPACE;  // the product needs more than the scratch array holds
 
     a.m = m;
@@ -133,6 +134,7 @@ extern "C" pb_status pb_spgemm_noalloc(const pb_csc *A, const pb_csr *B, pb_dtyp
     a.capacity = capacity;
     a.heavy = capacity / 2;
     a.nnzA = nnzA;
+    a.acol = acol;
     PB_NA_CUDA(cudaMemsetAsync(a.hdr, 0, sizeof(PlanHeader), s));
     PB_NA_CUDA(cudaMemsetAsync(err, 0, 64, s));
     PB_NA_CUDA(launch_symbolic(a, scan_tmp, s));
@@ -140,6 +142,11 @@ extern "C" pb_status pb_spgemm_noalloc(const pb_csc *A, const pb_csr *B, pb_dtyp
     PB_NA_CUDA(cudaMemcpyAsync(&hdr, a.hdr, sizeof(PlanHeader), cudaMemcpyDeviceToHost, s));
     PB_NA_CUDA(cudaStreamSynchronize(s));
     if (hdr.max_bin_count > 0x7fffffffull) return PB_ERR_UNSUPPORTED;
+    if (hdr.max_bin_count > (unsigned long long)capacity) {
+        PB_NA_CUDA(launch_symbolic_oversize(a, scan_tmp, s));
+        PB_NA_CUDA(cudaMemcpyAsync(&hdr, a.hdr, sizeof(PlanHeader), cudaMemcpyDeviceToHost, s));
+        PB_NA_CUDA(cudaStreamSynchronize(s));
+    }
 
     int32_t *over_chunk_bin = nullptr;
     int over_passes = 0;
@@ -151,7 +158,7 @@ extern "C" pb_status pb_spgemm_noalloc(const pb_csc *A, const pb_csr *B, pb_dtyp
     const int64_t nchunks = ceil_div<int64_t>(hdr.flop, chunk);
     int32_t *chunk_e = nullptr;
     if (!cv.take(chunk_e, 4 * ((size_t)nchunks + 1))) return PB_ERR_WORKSPACE;
-    PB_NA_CUDA(launch_chunk_table(a.F, A->colptr, B->rowptr, k, nnzA, nchunks, chunk, chunk_e, acol, s));
+    PB_NA_CUDA(launch_chunk_table(a, nchunks, chunk, chunk_e, s));
 
     // ---- numeric workspace -----------------------------------------------------------
     const size_t tb = (dtype == PB_F64) ? 8 : 4;

@@ -19,30 +19,49 @@ namespace pb {
 
 namespace {
 
-__global__ void k_flop_per_k(int32_t k, const int32_t *colptrA, const int32_t *rowptrB, int64_t *F) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < k; i += (int64_t)gridDim.x * blockDim.x) {
-        int64_t la = (int64_t)colptrA[i + 1] - colptrA[i];
-        int64_t lb = (int64_t)rowptrB[i + 1] - rowptrB[i];
-        F[i] = la * lb;
+// One thread per column k: f_k = nnz(A(:,k)) * nnz(B(k,:)) (Alg. 3), and the
+// column index of each of its A entries; columns with more than LONG_COL
+// entries are listed for a warp-wide pass instead.
+constexpr int LONG_COL = 32;
+
+__global__ void k_flop_per_k(int32_t k, const int32_t *colptrA, const int32_t *rowptrB, int64_t *F, int32_t *acol,
+                             int32_t *long_cols, uint32_t *n_long) {
+    for (int64_t col = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; col < k; col += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t a0 = colptrA[col], a1 = colptrA[col + 1];
+        F[col] = (int64_t)(a1 - a0) * ((int64_t)rowptrB[col + 1] - rowptrB[col]);
+        if (a1 - a0 > LONG_COL) {
+            long_cols[atomicAdd(n_long, 1u)] = (int32_t)col;
+        } else {
+            for (int32_t e = a0; e < a1; ++e) acol[e] = (int32_t)col;
+        }
     }
 }
 
-// One warp per column k: every A(i,k) adds nnz(B(k,:)) to row i.
-__global__ void k_row_flop(int32_t k, const int32_t *colptrA, const int32_t *rowidxA, const int32_t *rowptrB,
-                           int64_t *R) {
+// One warp per listed long column: the column index of each of its entries.
+__global__ void k_acol_long(const int32_t *colptrA, const int32_t *long_cols, const uint32_t *n_long, int32_t *acol) {
     const int lane = threadIdx.x & 31;
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t col = warp; col < k; col += nwarps) {
-        const int32_t a0 = colptrA[col], a1 = colptrA[col + 1];
+    const int64_t n = *n_long;
+    for (int64_t i = warp; i < n; i += nwarps) {
+        const int32_t col = long_cols[i];
+        for (int32_t e = colptrA[col] + lane; e < colptrA[col + 1]; e += 32) acol[e] = col;
+    }
+}
+
+// Every A(i,k) adds nnz(B(k,:)) to row i (the per-row form of Alg. 3); one
+// thread per A entry.
+__global__ void k_row_flop(int64_t nnzA, const int32_t *acol, const int32_t *rowidxA, const int32_t *rowptrB,
+                           int64_t *R) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nnzA; e += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t col = acol[e];
         const int64_t lb = (int64_t)rowptrB[col + 1] - rowptrB[col];
-        if (lb == 0) continue;
-        for (int32_t e = a0 + lane; e < a1; e += 32)
-            atomicAdd(reinterpret_cast<unsigned long long *>(&R[rowidxA[e]]), (unsigned long long)lb);
+        if (lb) atomicAdd(reinterpret_cast<unsigned long long *>(&R[rowidxA[e]]), (unsigned long long)lb);
     }
 }
 
 __global__ void k_max_light(int32_t m, const int64_t *R, int64_t heavy, PlanHeader *hdr) {
+    __shared__ unsigned long long wmax[32];
     unsigned long long best = 0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
         int64_t r = R[i + 1] - R[i];
@@ -53,7 +72,12 @@ __global__ void k_max_light(int32_t m, const int64_t *R, int64_t heavy, PlanHead
         unsigned long long t = __shfl_down_sync(FULL, best, o);
         best = t > best ? t : best;
     }
-    if ((threadIdx.x & 31) == 0 && best) atomicMax(&hdr->max_light_row, best);
+    if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = best;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) best = wmax[w] > best ? wmax[w] : best;
+        if (best) atomicMax(&hdr->max_light_row, best);
+    }
 }
 
 __device__ inline bool is_heavy(const int64_t *R, int64_t i, int64_t heavy) { return R[i + 1] - R[i] > heavy; }
@@ -138,20 +162,18 @@ __global__ void k_over_list(const int64_t *R, const int32_t *bin_row, int64_t ca
     }
 }
 
-// ainfo[e] = rowinfo[rowidxA[e]]: the bin and key high part of every A entry.
-__global__ void k_ainfo(int64_t nnz, const int32_t *rowidxA, const uint64_t *rowinfo, uint64_t *ainfo) {
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nnz; e += (int64_t)gridDim.x * blockDim.x)
-        ainfo[e] = rowinfo[rowidxA[e]];
-}
 
-__global__ void k_finish_header(const int64_t *F, int32_t k, int32_t m, const int64_t *bin_off,
+__global__ void k_finish_header(const int64_t *F, int32_t k, int32_t m, const int64_t *R, const int64_t *bin_off,
                                 const int64_t *over_scan, const int64_t *over_chunk_off,
                                 const int64_t *over_tuple_off, PlanHeader *hdr) {
     hdr->flop = F[k];
     hdr->tuples_padded = bin_off[hdr->nbins];
-    hdr->n_oversize = over_scan[m];
-    hdr->over_chunks = over_chunk_off[m];
-    hdr->over_tuples = over_tuple_off[m];
+    if (R[m] != F[k]) hdr->max_bin_count = ~0ull;  // per-row counts disagree with Alg. 3: reject
+    if (over_scan) {
+        hdr->n_oversize = over_scan[m];
+        hdr->over_chunks = over_chunk_off[m];
+        hdr->over_tuples = over_tuple_off[m];
+    }
 }
 
 __global__ void k_over_chunk_map(const int64_t *over_chunk_off, int64_t n_over, int32_t *over_chunk_bin) {
@@ -159,34 +181,32 @@ __global__ void k_over_chunk_map(const int64_t *over_chunk_off, int64_t n_over, 
         for (int64_t c = over_chunk_off[o]; c < over_chunk_off[o + 1]; ++c) over_chunk_bin[c] = (int32_t)o;
 }
 
-// Expand work items at A-entry granularity.  The runs of tuples of the A
-// entries tile [0, flop) in CSC order: entry j of column k owns
-// [F[k] + j*lb, F[k] + (j+1)*lb) with lb = nnz(B(k,:)).  Work item c holds the
-// entries whose run starts in [c*chunk, (c+1)*chunk): chunk_e[c] is the first
-// of them.  Also records the column of every A entry (acol).
-__global__ void k_chunk_table(const int64_t *F, const int32_t *colptrA, const int32_t *rowptrB, int32_t k,
-                              int64_t chunk, int32_t *chunk_e, int32_t *acol) {
-    const int lane = threadIdx.x & 31;
-    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t col = warp; col < k; col += nwarps) {
-        const int32_t a0 = colptrA[col], la = colptrA[col + 1] - a0;
+// Per A entry, once the bins are known:
+//   ainfo[e] = rowinfo[rowidxA[e]] (bin and key high part of the entry's row);
+//   expand work items at A-entry granularity.  The runs of tuples of the A
+//   entries tile [0, flop) in CSC order: entry j of column k owns
+//   [F[k] + j*lb, F[k] + (j+1)*lb) with lb = nnz(B(k,:)).  Work item c holds the
+//   entries whose run starts in [c*chunk, (c+1)*chunk): chunk_e[c] is the first.
+__global__ void k_entry_pass(int64_t nnzA, const int32_t *acol, const int32_t *rowidxA, const uint64_t *rowinfo,
+                             const int64_t *F, const int32_t *colptrA, const int32_t *rowptrB, int64_t chunk,
+                             uint64_t *ainfo, int32_t *chunk_e) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nnzA; e += (int64_t)gridDim.x * blockDim.x) {
+        ainfo[e] = rowinfo[rowidxA[e]];
+        const int32_t col = acol[e];
         const int64_t lb = (int64_t)rowptrB[col + 1] - rowptrB[col];
-        for (int32_t j = lane; j < la; j += 32) {
-            const int32_t e = a0 + j;
-            acol[e] = (int32_t)col;
-            if (lb == 0) continue;
-            const int64_t s = F[col] + (int64_t)j * lb, r = s + lb;
-            for (int64_t c = ceil_div<int64_t>(s, chunk); c * chunk < r; ++c) chunk_e[c] = (c * chunk == s) ? e : e + 1;
-        }
+        if (lb == 0) continue;
+        const int64_t s = F[col] + (e - colptrA[col]) * lb, r = s + lb;
+        for (int64_t c = ceil_div<int64_t>(s, chunk); c * chunk < r; ++c) chunk_e[c] = (c * chunk == s) ? (int32_t)e : (int32_t)(e + 1);
     }
 }
 
 __global__ void k_set_i32(int32_t *p, int32_t v) { *p = v; }
 
+// Grid of a grid-stride kernel: enough blocks to fill the GPU, not one per item
+// (tiny blocks cost more to launch and retire than their work).
 unsigned grid_for(int64_t n, int threads) {
     int64_t g = ceil_div<int64_t>(n > 0 ? n : 1, threads);
-    if (g > 65535ll * 32) g = 65535ll * 32;
+    if (g > 4096) g = 4096;
     return (unsigned)g;
 }
 
@@ -195,12 +215,14 @@ unsigned grid_for(int64_t n, int threads) {
 cudaError_t launch_symbolic(const SymbolicArgs &a, int64_t *scan_tmp, cudaStream_t s) {
     cudaError_t e;
     const int T = 256;
-    // 1. per-k flop and its prefix (Alg. 3)
-    k_flop_per_k<<<grid_for(a.k, T), T, 0, s>>>(a.k, a.colptrA, a.rowptrB, a.F);
+    // 1. per-k flop and its prefix (Alg. 3); column of every A entry
+    if ((e = cudaMemsetAsync(a.n_long, 0, sizeof(uint32_t), s)) != cudaSuccess) return e;
+    k_flop_per_k<<<grid_for(a.k, T), T, 0, s>>>(a.k, a.colptrA, a.rowptrB, a.F, a.acol, a.long_cols, a.n_long);
+    k_acol_long<<<grid_for((int64_t)a.k * 32, T), T, 0, s>>>(a.colptrA, a.long_cols, a.n_long, a.acol);
     if ((e = scan_i64(a.F, a.k, scan_tmp, s)) != cudaSuccess) return e;
     // 2. per-row flop (Sec. III-B) and its prefix
     if ((e = cudaMemsetAsync(a.R, 0, sizeof(int64_t) * ((size_t)a.m + 1), s)) != cudaSuccess) return e;
-    k_row_flop<<<grid_for((int64_t)a.k * 32, T), T, 0, s>>>(a.k, a.colptrA, a.rowidxA, a.rowptrB, a.R);
+    k_row_flop<<<grid_for(a.nnzA, T), T, 0, s>>>(a.nnzA, a.acol, a.rowidxA, a.rowptrB, a.R);
     if ((e = scan_i64(a.R, a.m, scan_tmp, s)) != cudaSuccess) return e;
     // 3. bins
     k_max_light<<<grid_for(a.m, T), T, 0, s>>>(a.m, a.R, a.heavy, a.hdr);
@@ -214,9 +236,17 @@ cudaError_t launch_symbolic(const SymbolicArgs &a, int64_t *scan_tmp, cudaStream
     if ((e = cudaMemsetAsync(a.bin_off, 0, sizeof(int64_t) * ((size_t)a.m + 2), s)) != cudaSuccess) return e;
     k_bin_sizes<<<grid_for(a.m, T), T, 0, s>>>(a.R, a.bin_row, a.capacity, a.hdr, a.bin_off);
     if ((e = scan_i64(a.bin_off, a.m, scan_tmp, s)) != cudaSuccess) return e;
-    // 5. bin and key high part of every A entry
-    k_ainfo<<<grid_for(a.nnzA, T), T, 0, s>>>(a.nnzA, a.rowidxA, a.rowinfo, a.ainfo);
-    // 6. oversize bins (single rows above the on-chip capacity): list, work items, scratch offsets
+    k_finish_header<<<1, 1, 0, s>>>(a.F, a.k, a.m, a.R, a.bin_off, nullptr, nullptr, nullptr, a.hdr);
+    count_launches(9);  // the non-scan kernels above
+    return cudaGetLastError();
+}
+
+// Oversize bins (single rows above the on-chip capacity): their list, work
+// items and scratch offsets.  Only needed when the header's largest bin count
+// exceeds the capacity.
+cudaError_t launch_symbolic_oversize(const SymbolicArgs &a, int64_t *scan_tmp, cudaStream_t s) {
+    cudaError_t e;
+    const int T = 256;
     const size_t mb = sizeof(int64_t) * ((size_t)a.m + 1);
     if ((e = cudaMemsetAsync(a.over_scan, 0, mb, s)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(a.over_chunk_off, 0, mb, s)) != cudaSuccess) return e;
@@ -227,9 +257,9 @@ cudaError_t launch_symbolic(const SymbolicArgs &a, int64_t *scan_tmp, cudaStream
                                                 a.over_chunk_off, a.over_tuple_off);
     if ((e = scan_i64(a.over_chunk_off, a.m, scan_tmp, s)) != cudaSuccess) return e;
     if ((e = scan_i64(a.over_tuple_off, a.m, scan_tmp, s)) != cudaSuccess) return e;
-    k_finish_header<<<1, 1, 0, s>>>(a.F, a.k, a.m, a.bin_off, a.over_scan, a.over_chunk_off, a.over_tuple_off,
-                                    a.hdr);
-    count_launches(11);  // the non-scan kernels above
+    k_finish_header<<<1, 1, 0, s>>>(a.F, a.k, a.m, a.R, a.bin_off, a.over_scan, a.over_chunk_off,
+                                    a.over_tuple_off, a.hdr);
+    count_launches(3);
     return cudaGetLastError();
 }
 
@@ -241,14 +271,14 @@ cudaError_t launch_over_chunk_map(const int64_t *over_chunk_off, int64_t n_over,
     return cudaGetLastError();
 }
 
-cudaError_t launch_chunk_table(const int64_t *F, const int32_t *colptrA, const int32_t *rowptrB, int32_t k,
-                               int64_t nnzA, int64_t nchunks, int64_t chunk, int32_t *chunk_e, int32_t *acol,
+cudaError_t launch_chunk_table(const SymbolicArgs &a, int64_t nchunks, int64_t chunk, int32_t *chunk_e,
                                cudaStream_t s) {
     // chunk_e[nchunks] = nnzA closes the last work item
-    k_set_i32<<<1, 1, 0, s>>>(chunk_e + nchunks, (int32_t)nnzA);
+    k_set_i32<<<1, 1, 0, s>>>(chunk_e + nchunks, (int32_t)a.nnzA);
     count_launches(1);
-    if (k > 0) {
-        k_chunk_table<<<grid_for((int64_t)k * 32, 256), 256, 0, s>>>(F, colptrA, rowptrB, k, chunk, chunk_e, acol);
+    if (a.nnzA > 0) {
+        k_entry_pass<<<grid_for(a.nnzA, 256), 256, 0, s>>>(a.nnzA, a.acol, a.rowidxA, a.rowinfo, a.F, a.colptrA,
+                                                           a.rowptrB, chunk, a.ainfo, chunk_e);
         count_launches(1);
     }
     return cudaGetLastError();
