@@ -193,6 +193,87 @@ pb_status pb_set_phase_events(pb_handle *h, void *const *events);
 int64_t pb_kernel_launches(void);
 
 /*
+ * Batched products.  Running many independent products together has no
+ * counterpart in the paper; every product still goes through Alg. 3, the
+ * expand of Alg. 2, the bin sort of Sec. III-D and the merge of Sec. III-E.
+ *
+ * pb_spgemm_batch computes C[i] = A[i] * B[i] for 0 <= i < count as one pass:
+ * the products are laid out back to back (rows, columns of A and A entries
+ * each in one index space), bins never straddle two products, the look-back
+ * that places each bin's output restarts at each product's first bin, and the
+ * sort kernel writes every bin straight into its own product's C.  Symbolic
+ * kernels, one expand launch and one sort launch per bin-capacity level serve
+ * the whole batch with persistent grids.
+ *
+ * Parameters per product come from the handle's tuning table, keyed by the
+ * sparsity class (log2n, dclass):
+ *   log2n  = ceil(log2(max(A.nrows, 2)))
+ *   dclass = bit length of round(nnz(A) / max(A.ncols, 1)), i.e. 1 for d = 1,
+ *            2 for d = 2..3, 3 for 4..7, 4 for 8..15, 5 for 16..31, ...
+ * An untuned class uses bin_capacity 4096, rmax_log2 11, expand_chunk 4096.
+ *
+ * pb_spgemm_batch is asynchronous: it allocates nothing, never synchronises
+ * the host and makes no host-device copies, so a call can be captured into a
+ * CUDA graph and replayed.  The products' sizes and device pointers are baked
+ * into the launches; a replay recomputes everything from the arrays' current
+ * contents.  The launch-parameter blocks describing the products take about
+ * 160 bytes per product.
+ *
+ *   workspace   device buffer, 256-byte aligned, at least the size
+ *               pb_spgemm_batch_query reports for these operands; scratch.
+ *   C[i]        as for pb_spgemm_numeric (no counting run): exactly one of
+ *               rowptr64 / rowptr32, cap >= nnz(C[i]) (the product's flop,
+ *               from the query, always suffices), nnz_dev optional.
+ *   device_status  DEVICE pointer to one int32 that receives, in stream
+ *               order after the last kernel, PB_OK or the device-detected
+ *               error of the batch: PB_ERR_OVERFLOW (a C[i] too small),
+ *               PB_ERR_WORKSPACE (tuples do not fit), PB_ERR_UNSUPPORTED (a
+ *               single row of some product has more tuples than that
+ *               product's bin capacity: run it with pb_spgemm_numeric),
+ *               PB_ERR_TIMEOUT.
+ * Limits: count <= 2^20; the sums over the batch of A.nrows, A.ncols and
+ * nnz(A) each below 2^31.
+ * Errors (returned): INVALID_ARG, SHAPE, UNSUPPORTED_DTYPE, UNSUPPORTED, CUDA.
+ */
+typedef struct pb_batch_tune {
+    int32_t log2n;         /* class key */
+    int32_t dclass;        /* class key */
+    int32_t bin_capacity;  /* tuples per bin sorted on chip: 2048, 4096 or 8192 */
+    int32_t rmax_log2;     /* a bin spans at most 2^rmax_log2 rows (1..11) */
+    int32_t expand_chunk;  /* tuples per expand work item (multiple of 32, >= 256) */
+    int32_t reserved;
+} pb_batch_tune;
+
+/* Workspace for pb_spgemm_batch on these operands and, per product (host
+ * arrays of count entries, either may be NULL), its flop (Alg. 3; a C
+ * capacity that always suffices) and its largest per-row flop (a product
+ * whose largest row exceeds its bin capacity is rejected by the batch).
+ * Synchronises `stream` once; allocates a temporary buffer through the
+ * handle's allocator. */
+pb_status pb_spgemm_batch_query(pb_handle *h, int32_t count, const pb_csc *A, const pb_csr *B, pb_dtype dtype,
+                                pb_stream_t stream, size_t *workspace_bytes, int64_t *flop,
+                                int64_t *max_row_flop);
+
+pb_status pb_spgemm_batch(pb_handle *h, int32_t count, const pb_csc *A, const pb_csr *B, pb_csr_out *C,
+                          pb_dtype dtype, void *workspace, size_t ws_bytes, pb_stream_t stream,
+                          int32_t *device_status);
+
+/* Autotuner: for every sparsity class present in the batch, times candidate
+ * (bin_capacity, rmax_log2, expand_chunk) settings on that class's products
+ * (CUDA events, `reps` timed runs each after one warm-up) and stores the
+ * fastest in the handle's tuning table.  Synchronous.  Uses C and the
+ * workspace exactly like pb_spgemm_batch (C receives the products under the
+ * chosen settings); allocates a 256-byte status word through the handle's
+ * allocator.  Settings whose run reports a device error are skipped. */
+pb_status pb_batch_autotune(pb_handle *h, int32_t count, const pb_csc *A, const pb_csr *B, pb_csr_out *C,
+                            pb_dtype dtype, void *workspace, size_t ws_bytes, pb_stream_t stream, int32_t reps);
+
+/* Read / replace the tuning table.  get writes up to `cap` entries and the
+ * table's size to *n; set replaces the table (entries are validated). */
+pb_status pb_batch_get_tuning(const pb_handle *h, pb_batch_tune *out, int32_t cap, int32_t *n);
+pb_status pb_batch_set_tuning(pb_handle *h, const pb_batch_tune *entries, int32_t n);
+
+/*
  * No-allocation entry point (the paper has no counterpart; this serves callers).
  *
  * Some callers cannot allocate device memory where they need a product: code

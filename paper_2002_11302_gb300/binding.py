@@ -58,6 +58,11 @@ class _Config(ctypes.Structure):
                 ("max_tuple_bytes", ctypes.c_int64), ("reserved1", ctypes.c_int64)]
 
 
+class _BatchTune(ctypes.Structure):
+    _fields_ = [("log2n", ctypes.c_int32), ("dclass", ctypes.c_int32), ("bin_capacity", ctypes.c_int32),
+                ("rmax_log2", ctypes.c_int32), ("expand_chunk", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
 _ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
 _FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
 
@@ -84,6 +89,14 @@ SIGNATURES = {
     "pb_kernel_launches": (_I64, []),
     "pb_spgemm_noalloc": (ctypes.c_int, [ctypes.POINTER(_CSC), ctypes.POINTER(_CSR), ctypes.c_int,
                                          ctypes.POINTER(_CSROut), _VP, ctypes.POINTER(ctypes.c_int)]),
+    "pb_spgemm_batch_query": (ctypes.c_int, [_VP, _I32, ctypes.POINTER(_CSC), ctypes.POINTER(_CSR), ctypes.c_int,
+                                             _VP, ctypes.POINTER(_SZ), ctypes.POINTER(_I64), ctypes.POINTER(_I64)]),
+    "pb_spgemm_batch": (ctypes.c_int, [_VP, _I32, ctypes.POINTER(_CSC), ctypes.POINTER(_CSR),
+                                       ctypes.POINTER(_CSROut), ctypes.c_int, _VP, _SZ, _VP, _VP]),
+    "pb_batch_autotune": (ctypes.c_int, [_VP, _I32, ctypes.POINTER(_CSC), ctypes.POINTER(_CSR),
+                                         ctypes.POINTER(_CSROut), ctypes.c_int, _VP, _SZ, _VP, _I32]),
+    "pb_batch_get_tuning": (ctypes.c_int, [_VP, ctypes.POINTER(_BatchTune), _I32, ctypes.POINTER(_I32)]),
+    "pb_batch_set_tuning": (ctypes.c_int, [_VP, ctypes.POINTER(_BatchTune), _I32]),
 }
 
 _lib = None
@@ -390,3 +403,96 @@ def spgemm(A: CscMatrix, B: CsrMatrix, dtype: int = PB_F64, config: Optional[_Co
         raise PBError(st, "device-side error in the numeric phase")
     nnz = int(C.rowptr[-1].item())
     return CsrMatrix(C.nrows, C.ncols, C.rowptr, C.colidx[:nnz], C.val[:nnz])
+
+
+# ---------------------------------------------------------------------------
+# Batched products (pb_spgemm_batch).
+# ---------------------------------------------------------------------------
+class Batch:
+    """A batch of independent products C[i] = A[i] * B[i] with its workspace.
+
+    The struct arrays handed to the library are built once, so repeated
+    run() calls (or a CUDA graph captured around one) cost only the launches.
+    query() sizes the workspace and gives each product's flop (the C capacity
+    that always suffices) and its largest per-row flop.
+    """
+
+    def __init__(self, As, Bs, dtype: int = PB_F64, handle: Optional[Handle] = None, rowptr64: bool = True,
+                 caps=None, stream=None):
+        self.handle = handle or default_handle()
+        self.lib = self.handle.lib
+        self.dtype = dtype
+        self.As, self.Bs = list(As), list(Bs)
+        n = len(self.As)
+        if len(self.Bs) != n:
+            raise PBError(1, "A and B lists differ in length")
+        self.count = n
+        self._cA = (_CSC * max(n, 1))(*[a._c() for a in self.As])
+        self._cB = (_CSR * max(n, 1))(*[b._c() for b in self.Bs])
+        ws = _SZ()
+        self.flop = np.zeros(max(n, 1), dtype=np.int64)
+        self.max_row = np.zeros(max(n, 1), dtype=np.int64)
+        _check(self.lib, self.handle.ptr, self.lib.pb_spgemm_batch_query(
+            self.handle.ptr, n, self._cA, self._cB, dtype, _stream_ptr(stream), ctypes.byref(ws),
+            self.flop.ctypes.data_as(ctypes.POINTER(_I64)), self.max_row.ctypes.data_as(ctypes.POINTER(_I64))))
+        self.flop, self.max_row = self.flop[:n], self.max_row[:n]
+        self.workspace_bytes = int(ws.value) + 256
+        dev = torch.device("cuda")
+        self.workspace = torch.empty(max(self.workspace_bytes, 256), dtype=torch.uint8, device=dev)
+        self.device_status = torch.zeros(1, dtype=torch.int32, device=dev)
+        self.nnz = torch.zeros(max(n, 1), dtype=torch.int64, device=dev)
+        caps = self.flop if caps is None else caps
+        self.C = []
+        outs = []
+        for i in range(n):
+            cap = max(int(caps[i]), 1)
+            C = CsrMatrix(self.As[i].nrows, self.Bs[i].ncols,
+                          torch.empty(self.As[i].nrows + 1, dtype=torch.int64 if rowptr64 else torch.int32,
+                                      device=dev),
+                          torch.empty(cap, dtype=torch.int32, device=dev),
+                          torch.empty(cap, dtype=_OUT_DTYPE[dtype], device=dev))
+            self.C.append(C)
+            outs.append(_CSROut(C.nrows, C.ncols, cap, C.rowptr.data_ptr() if rowptr64 else None,
+                                None if rowptr64 else C.rowptr.data_ptr(), C.colidx.data_ptr(), C.val.data_ptr(),
+                                self.nnz.data_ptr() + 8 * i))
+        self._cC = (_CSROut * max(n, 1))(*outs)
+
+    def run(self, stream=None) -> None:
+        """Launch the batch on `stream` (asynchronous; no allocation, no host sync)."""
+        _check(self.lib, self.handle.ptr, self.lib.pb_spgemm_batch(
+            self.handle.ptr, self.count, self._cA, self._cB, self._cC, self.dtype, self.workspace.data_ptr(),
+            self.workspace_bytes, _stream_ptr(stream), self.device_status.data_ptr()))
+
+    def status(self) -> int:
+        """Device status of the last run (synchronises)."""
+        return int(self.device_status.item())
+
+    def autotune(self, reps: int = 3, stream=None) -> None:
+        _check(self.lib, self.handle.ptr, self.lib.pb_batch_autotune(
+            self.handle.ptr, self.count, self._cA, self._cB, self._cC, self.dtype, self.workspace.data_ptr(),
+            self.workspace_bytes, _stream_ptr(stream), reps))
+
+    def result(self, i: int) -> CsrMatrix:
+        """Product i trimmed to its nnz (synchronises)."""
+        C = self.C[i]
+        k = int(self.nnz[i].item())
+        return CsrMatrix(C.nrows, C.ncols, C.rowptr, C.colidx[:k], C.val[:k])
+
+
+def get_tuning(handle: Optional[Handle] = None):
+    """The handle's batch tuning table as a list of dicts."""
+    h = handle or default_handle()
+    n = _I32()
+    _check(h.lib, h.ptr, h.lib.pb_batch_get_tuning(h.ptr, None, 0, ctypes.byref(n)))
+    arr = (_BatchTune * max(n.value, 1))()
+    _check(h.lib, h.ptr, h.lib.pb_batch_get_tuning(h.ptr, arr, n.value, ctypes.byref(n)))
+    keys = ("log2n", "dclass", "bin_capacity", "rmax_log2", "expand_chunk")
+    return [{k: int(getattr(arr[i], k)) for k in keys} for i in range(n.value)]
+
+
+def set_tuning(entries, handle: Optional[Handle] = None) -> None:
+    h = handle or default_handle()
+    arr = (_BatchTune * max(len(entries), 1))(
+        *[_BatchTune(e["log2n"], e["dclass"], e["bin_capacity"], e["rmax_log2"], e["expand_chunk"], 0)
+          for e in entries])
+    _check(h.lib, h.ptr, h.lib.pb_batch_set_tuning(h.ptr, arr, len(entries)))

@@ -9,19 +9,9 @@
 #include <vector>
 
 #include "pb_common.cuh"
+#include "pb_host.h"
 
 using namespace pb;
-
-struct pb_handle {
-    int device = 0;
-    int num_sms = 0;
-    pb_alloc_fn alloc = nullptr;
-    pb_free_fn free_fn = nullptr;
-    void *ctx = nullptr;
-    std::string last_error;
-    cudaEvent_t phase_ev[4] = {nullptr, nullptr, nullptr, nullptr};
-    bool phase_on = false;
-};
 
 namespace pb {
 static std::atomic<int64_t> g_launches{0};
@@ -134,6 +124,12 @@ void free_plan_memory(pb_plan *p) {
 }
 
 }  // namespace
+
+namespace pb {
+pb_status host_fail(pb_handle *h, pb_status st, const std::string &msg) { return fail(h, st, msg); }
+pb_status host_cuda_fail(pb_handle *h, cudaError_t e, const char *where) { return cuda_fail(h, e, where); }
+pb_status host_check_operands(pb_handle *h, const pb_csc *A, const pb_csr *B) { return check_operands(h, A, B); }
+}  // namespace pb
 
 extern "C" {
 

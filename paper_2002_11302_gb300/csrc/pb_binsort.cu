@@ -30,6 +30,21 @@ namespace {
 constexpr int RMAX = 1 << RMAX_LOG2;  // max rows of one bin (symbolic cuts bins at multiples of this)
 constexpr int SMALL_BUCKET = 32;
 
+// Output of the bin being processed, for batched products (the product's C).
+struct BinOut {
+    int64_t *rowptr64;
+    int32_t *rowptr32;
+    int32_t *colidx;
+    void *valC;
+    int64_t *nnz_dev;
+    int64_t cap;
+    int64_t first;   // the product's first bin: its look-back chain starts there
+    int32_t rbase;   // global row of the product's row 0
+    int32_t m;
+    int32_t colbits;
+    int32_t last;    // the product's last bin
+};
+
 template <int CAP, int THREADS, class TV>
 struct SortSmem {
     static constexpr int NW = THREADS / 32;
@@ -49,6 +64,7 @@ struct SortSmem {
     int64_t prefix;
     uint32_t big;
     int32_t ok;
+    BinOut out;
 };
 
 __device__ inline void write_rowptr(const NumericArgs &p, int64_t row, int64_t v) {
@@ -56,6 +72,13 @@ __device__ inline void write_rowptr(const NumericArgs &p, int64_t row, int64_t v
         p.rowptr64[row] = v;
     else
         p.rowptr32[row] = (int32_t)v;
+}
+
+__device__ inline void write_rowptr(const BinOut &o, int64_t row, int64_t v) {
+    if (o.rowptr64)
+        o.rowptr64[row] = v;
+    else
+        o.rowptr32[row] = (int32_t)v;
 }
 
 // Exclusive scan in place of cnt[0..n), blocked per thread; all threads.
@@ -170,12 +193,14 @@ __device__ inline int64_t lookback_warp(uint64_t *status, int64_t b, uint64_t ag
 // closer than the nearest inclusive prefix has published its count; the
 // counts up to that prefix are then summed.  Returns the exclusive prefix
 // (all threads); thread 0 publishes this bin's aggregate and inclusive prefix.
+// The chain starts at bin `first` (0 for one product; a product's first bin in
+// a batch): bins before it count as an inclusive prefix of 0.
 template <int THREADS>
 __device__ inline int64_t lookback_block(uint64_t *status, int64_t b, uint64_t agg, uint32_t *err, int64_t *scratch,
-                                         int32_t *marks) {
+                                         int32_t *marks, int64_t first) {
     const int tid = threadIdx.x;
-    if (b == 0) {
-        if (tid == 0) st_release_u64(&status[0], LB_PREFIX | agg);
+    if (b == first) {
+        if (tid == 0) st_release_u64(&status[b], LB_PREFIX | agg);
         return 0;
     }
     if (tid == 0) st_release_u64(&status[b], LB_AGGREGATE | agg);
@@ -200,7 +225,7 @@ __device__ inline int64_t lookback_block(uint64_t *status, int64_t b, uint64_t a
         }
         __syncthreads();
         const int64_t idx = j - tid;
-        const uint64_t v = (idx >= 0) ? ld_acquire_u64(&status[idx]) : LB_PREFIX;  // before bin 0: prefix 0
+        const uint64_t v = (idx >= first) ? ld_acquire_u64(&status[idx]) : LB_PREFIX;  // before the chain: 0
         if ((v & ~LB_VALUE_MASK) == LB_PREFIX) atomicMin(&marks[0], tid);
         if ((v >> LB_FLAG_SHIFT) == 0) atomicMin(&marks[1], tid);
         __syncthreads();
@@ -276,7 +301,9 @@ __device__ void stream_oversize_bin(const NumericArgs &p, int64_t b, int32_t row
     __syncthreads();
 }
 
-template <int CAP, int THREADS, class TV, class OV>
+// BATCH: bins of the products of a batch that share one capacity level; each
+// bin writes into its own product's C (taken from the product's descriptor).
+template <int CAP, int THREADS, class TV, class OV, bool BATCH>
 __global__ void __launch_bounds__(THREADS, (THREADS <= 256 ? 4 : (THREADS <= 512 ? 2 : 1))) k_binsort(const NumericArgs p) {
     using S = SortSmem<CAP, THREADS, TV>;
     constexpr int NW = THREADS / 32;
@@ -290,25 +317,39 @@ __global__ void __launch_bounds__(THREADS, (THREADS <= 256 ? 4 : (THREADS <= 512
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const TV *__restrict__ gvals = static_cast<const TV *>(p.vals);
     OV *__restrict__ valC = static_cast<OV *>(p.valC);
-    const uint32_t colmask = (p.colbits >= 32) ? 0xffffffffu : ((1u << p.colbits) - 1u);
+    int colbits = p.colbits;
+    uint32_t colmask = (p.colbits >= 32) ? 0xffffffffu : ((1u << p.colbits) - 1u);
 
     if (tid == 0) mbar_init(&sm.bar, 1);
     __syncthreads();
     uint32_t phase = 0;
+    int64_t bin_lo = p.bin_lo, bin_hi = p.bin_hi, nbins = p.nbins;
+    if constexpr (BATCH) {
+        if (*p.err & DEV_ERR_BATCH_FATAL) return;
+        bin_lo = p.bhdr->level_bins[p.level];
+        bin_hi = p.bhdr->level_bins[p.level + 1];
+        nbins = p.bhdr->nbins;
+    }
 
     while (true) {
-        if (tid == 0) sm.bin = p.bin_lo + (int64_t)atomicAdd(p.ticket, 1u);
+        if (tid == 0) sm.bin = bin_lo + (int64_t)atomicAdd(p.ticket, 1u);
         fence_proxy_async_smem();  // earlier generic smem accesses before the next bulk copy
         __syncthreads();
         const int64_t b = sm.bin;
-        if (b >= p.bin_hi) break;
+        if (b >= bin_hi) break;
         const int32_t row0 = p.bin_row[b], row1 = p.bin_row[b + 1];
         const int64_t off = p.bin_off[b] - p.tuple_base;  // the buffer holds this panel's tuples
-        const int64_t Nfull = p.R[row1] - p.R[row0];
+        int64_t Nfull = p.R[row1] - p.R[row0];
         if (Nfull > CAP) {
-            stream_oversize_bin<THREADS, TV, OV>(p, b, row0, row1, off, Nfull, colmask, sm.scratch, &sm.prefix,
-                                                 &sm.ok);
-            continue;
+            if constexpr (BATCH) {
+                // the symbolic phase never cuts such a bin for a batch; record it and skip the tuples
+                if (tid == 0) atomicOr(p.err, DEV_ERR_CAPACITY);
+                Nfull = 0;
+            } else {
+                stream_oversize_bin<THREADS, TV, OV>(p, b, row0, row1, off, Nfull, colmask, sm.scratch,
+                                                     &sm.prefix, &sm.ok);
+                continue;
+            }
         }
         int N = (int)Nfull;
         const int rows_b = row1 - row0;
@@ -319,6 +360,24 @@ __global__ void __launch_bounds__(THREADS, (THREADS <= 256 ? 4 : (THREADS <= 512
             mbar_arrive_expect_tx(&sm.bar, n4 * 4u + n4 * (uint32_t)sizeof(TV));
             bulk_g2s(sm.kin, p.keys + off, n4 * 4u, &sm.bar);
             bulk_g2s(sm.vin, gvals + off, n4 * (uint32_t)sizeof(TV), &sm.bar);
+        }
+        if constexpr (BATCH) {
+            if (tid == 0) {  // the bin's product, fetched while the copies are in flight
+                const int32_t q = p.bin_prod[b];
+                const BatchDesc &d = p.desc[q];
+                BinOut &o = sm.out;
+                o.rowptr64 = d.rowptr64;
+                o.rowptr32 = d.rowptr32;
+                o.colidx = d.colidxC;
+                o.valC = d.valC;
+                o.nnz_dev = d.nnz_dev;
+                o.cap = d.capC;
+                o.first = p.prod[q].first_bin;
+                o.rbase = d.mstart;
+                o.m = d.m;
+                o.colbits = d.colbits;
+                o.last = (b + 1 == nbins || p.bin_prod[b + 1] != q) ? 1 : 0;
+            }
         }
         for (int r = tid; r < rows_b; r += THREADS) sm.rowcnt[r] = 0;
         for (int i = tid; i <= CAP; i += THREADS) sm.cnt[i] = 0;
@@ -334,12 +393,16 @@ __global__ void __launch_bounds__(THREADS, (THREADS <= 256 ? 4 : (THREADS <= 512
             N = 0;
         }
 
+        if constexpr (BATCH) {
+            colbits = sm.out.colbits;
+            colmask = (colbits >= 32) ? 0xffffffffu : ((1u << colbits) - 1u);
+        }
         const uint32_t *sk = sm.skey;
         const uint16_t *si = sm.sidx;
         if (N > 0) {
             // Keys lie in [0, rows_b << colbits): the bucket of a key is its top
             // LOG_CAP significant bits.
-            const uint32_t kmax = (uint32_t)((((uint64_t)rows_b) << p.colbits) - 1u);
+            const uint32_t kmax = (uint32_t)((((uint64_t)rows_b) << colbits) - 1u);
             const int rbits = kmax ? 32 - __clz(kmax) : 0;
             const int shift = rbits > LOG_CAP ? rbits - LOG_CAP : 0;
             // ---- bucket pass (MSD on the top bits) -----------------------------------
@@ -459,7 +522,7 @@ __global__ void __launch_bounds__(THREADS, (THREADS <= 256 ? 4 : (THREADS <= 512
             const int q = base + lane;
             const bool head = q < s1 && (q == 0 || sk[q - 1] != sk[q]);
             wheads += __popc(__ballot_sync(FULL, head));
-            if (head) atomicAdd(&sm.rowcnt[sk[q] >> p.colbits], 1u);
+            if (head) atomicAdd(&sm.rowcnt[sk[q] >> colbits], 1u);
         }
         if (lane == 0) sm.wtot[warp] = wheads;
         __syncthreads();
@@ -471,18 +534,34 @@ __global__ void __launch_bounds__(THREADS, (THREADS <= 256 ? 4 : (THREADS <= 512
             U += t;
         }
         {
-            const int64_t P = lookback_block<THREADS>(p.status, b, (uint64_t)U, p.err, sm.scratch, sm.marks);
+            const int64_t first = BATCH ? sm.out.first : 0;
+            const int64_t P = lookback_block<THREADS>(p.status, b, (uint64_t)U, p.err, sm.scratch, sm.marks, first);
             if (tid == 0) {
-                int32_t good = p.count_only ? 0 : 1;
-                if (!p.count_only && (P + U > p.cap || (p.rowptr32 && P + U > 0x7fffffffll))) {
-                    atomicOr(p.err, DEV_ERR_OVERFLOW);
-                    good = 0;
-                }
-                sm.prefix = P;
-                sm.ok = good;
-                if (b == p.nbins - 1) {
-                    if (good) write_rowptr(p, p.m, P + U);
-                    if (p.nnz_dev) *p.nnz_dev = P + U;
+                if constexpr (BATCH) {
+                    const BinOut &o = sm.out;
+                    int32_t good = 1;
+                    if (P + U > o.cap || (o.rowptr32 && P + U > 0x7fffffffll)) {
+                        atomicOr(p.err, DEV_ERR_OVERFLOW);
+                        good = 0;
+                    }
+                    sm.prefix = P;
+                    sm.ok = good;
+                    if (o.last) {
+                        if (good) write_rowptr(o, o.m, P + U);
+                        if (o.nnz_dev) *o.nnz_dev = P + U;
+                    }
+                } else {
+                    int32_t good = p.count_only ? 0 : 1;
+                    if (!p.count_only && (P + U > p.cap || (p.rowptr32 && P + U > 0x7fffffffll))) {
+                        atomicOr(p.err, DEV_ERR_OVERFLOW);
+                        good = 0;
+                    }
+                    sm.prefix = P;
+                    sm.ok = good;
+                    if (b == p.nbins - 1) {
+                        if (good) write_rowptr(p, p.m, P + U);
+                        if (p.nnz_dev) *p.nnz_dev = P + U;
+                    }
                 }
             }
             __syncthreads();
@@ -496,7 +575,12 @@ __global__ void __launch_bounds__(THREADS, (THREADS <= 256 ? 4 : (THREADS <= 512
                     const int r = r0 + lane;
                     const uint32_t c = (r < rows_b) ? sm.rowcnt[r] : 0u;
                     const uint32_t inc = warp_inclusive_scan(c);
-                    if (r < rows_b) write_rowptr(p, row0 + r, P + carry + inc - c);
+                    if (r < rows_b) {
+                        if constexpr (BATCH)
+                            write_rowptr(sm.out, row0 - sm.out.rbase + r, P + carry + inc - c);
+                        else
+                            write_rowptr(p, row0 + r, P + carry + inc - c);
+                    }
                     carry += __shfl_sync(FULL, inc, 31);
                 }
             }
@@ -505,6 +589,11 @@ __global__ void __launch_bounds__(THREADS, (THREADS <= 256 ? 4 : (THREADS <= 512
         const int64_t P = sm.prefix;
         if (sm.ok) {
             // ---- merged entries in key order, coalesced across the warp ----------------
+            int32_t *colidxC = p.colidx;
+            if constexpr (BATCH) {
+                colidxC = sm.out.colidx;
+                valC = static_cast<OV *>(sm.out.valC);
+            }
             int64_t out = P + wbase;
             for (int base = s0; base < s1; base += 32) {
                 const int q = base + lane;
@@ -515,7 +604,7 @@ __global__ void __launch_bounds__(THREADS, (THREADS <= 256 ? 4 : (THREADS <= 512
                     double acc = (double)sm.vin[si[q]];
                     for (int r = q + 1; r < N && sk[r] == key; ++r) acc += (double)sm.vin[si[r]];
                     const int64_t o = out + __popc(hm & lanemask_lt());
-                    p.colidx[o] = (int32_t)(key & colmask);
+                    colidxC[o] = (int32_t)(key & colmask);
                     valC[o] = (OV)acc;
                 }
                 out += __popc(hm);
@@ -525,10 +614,10 @@ __global__ void __launch_bounds__(THREADS, (THREADS <= 256 ? 4 : (THREADS <= 512
     }
 }
 
-template <int CAP, int THREADS, class TV, class OV>
+template <int CAP, int THREADS, class TV, class OV, bool BATCH>
 cudaError_t run_binsort(const NumericArgs &a, cudaStream_t s) {
     using S = SortSmem<CAP, THREADS, TV>;
-    auto kern = k_binsort<CAP, THREADS, TV, OV>;
+    auto kern = k_binsort<CAP, THREADS, TV, OV, BATCH>;
     const size_t smem = sizeof(S);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -537,6 +626,7 @@ cudaError_t run_binsort(const NumericArgs &a, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
     int64_t grid = (int64_t)a.num_sms * per_sm;
+    // a batch's bin count is only known on the device: a.bin_hi - a.bin_lo bounds it
     if (grid > a.bin_hi - a.bin_lo) grid = a.bin_hi - a.bin_lo;
     if (grid < 1) return cudaSuccess;
     kern<<<(unsigned)grid, THREADS, smem, s>>>(a);
@@ -544,26 +634,33 @@ cudaError_t run_binsort(const NumericArgs &a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-template <class TV, class OV>
+template <class TV, class OV, bool BATCH>
 cudaError_t dispatch_cap(const NumericArgs &a, cudaStream_t s) {
     switch (a.capacity) {
-        case 2048: return run_binsort<2048, 256, TV, OV>(a, s);
-        case 4096: return run_binsort<4096, 512, TV, OV>(a, s);
-        case 8192: return run_binsort<8192, 1024, TV, OV>(a, s);
+        case 2048: return run_binsort<2048, 256, TV, OV, BATCH>(a, s);
+        case 4096: return run_binsort<4096, 512, TV, OV, BATCH>(a, s);
+        case 8192: return run_binsort<8192, 1024, TV, OV, BATCH>(a, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <bool BATCH>
+cudaError_t dispatch_dtype(const NumericArgs &a, cudaStream_t s) {
+    if (a.bin_hi <= a.bin_lo) return cudaSuccess;
+    switch (a.dtype) {
+        case PB_F64: return dispatch_cap<double, double, BATCH>(a, s);
+        case PB_F32: return dispatch_cap<float, float, BATCH>(a, s);
+        case PB_F64_F32TUPLE: return dispatch_cap<float, double, BATCH>(a, s);
         default: return cudaErrorInvalidValue;
     }
 }
 
 }  // namespace
 
-cudaError_t launch_binsort(const NumericArgs &a, cudaStream_t s) {
-    if (a.bin_hi <= a.bin_lo) return cudaSuccess;
-    switch (a.dtype) {
-        case PB_F64: return dispatch_cap<double, double>(a, s);
-        case PB_F32: return dispatch_cap<float, float>(a, s);
-        case PB_F64_F32TUPLE: return dispatch_cap<float, double>(a, s);
-        default: return cudaErrorInvalidValue;
-    }
-}
+cudaError_t launch_binsort(const NumericArgs &a, cudaStream_t s) { return dispatch_dtype<false>(a, s); }
+
+// a.bin_lo / a.bin_hi bound the level's bins (grid size only); the kernel reads
+// the exact range from a.bhdr.  a.ticket is the level's own counter.
+cudaError_t launch_binsort_batch(const NumericArgs &a, cudaStream_t s) { return dispatch_dtype<true>(a, s); }
 
 }  // namespace pb

@@ -16,7 +16,11 @@ enum : uint32_t {
     DEV_ERR_OVERFLOW = 1u << 0,   // nnz(C) > C.cap or an int32 row pointer would overflow
     DEV_ERR_TIMEOUT = 1u << 1,    // a bounded wait (look-back, mbarrier) gave up
     DEV_ERR_CAPACITY = 1u << 2,   // a bin held more tuples than the plan sized it for
+    DEV_ERR_WORKSPACE = 1u << 3,  // batch: the tuples do not fit the caller's workspace
+    DEV_ERR_HEAVY_ROW = 1u << 4,  // batch: one row has more tuples than its bin capacity
 };
+// Errors after which the batched kernels do no further work.
+constexpr uint32_t DEV_ERR_BATCH_FATAL = DEV_ERR_WORKSPACE | DEV_ERR_HEAVY_ROW;
 
 // Look-back status of one bin: two flag bits over a 62-bit count.
 constexpr uint64_t LB_FLAG_SHIFT = 62;
@@ -224,6 +228,46 @@ cudaError_t launch_over_chunk_map(const int64_t *over_chunk_off, int64_t n_over,
                                   cudaStream_t s);
 cudaError_t launch_oversize(const OversizeArgs &a, int passes, int dtype, int num_sms, cudaStream_t s);
 
+// ---------------------------------------------------------------------------
+// Batched products (pb_spgemm_batch).  The products are laid out back to back
+// in three global index spaces: rows (of A and C), columns of A (= rows of B)
+// and A entries.  Each space is cut into tiles of BATCH_TILE elements that never
+// straddle two products; tile_*[p] is the first tile of product p.
+// ---------------------------------------------------------------------------
+constexpr int BATCH_TILE = 1024;
+
+struct BatchDesc {
+    const int32_t *colptrA, *rowidxA;
+    const void *valA;
+    const int32_t *rowptrB, *colidxB;
+    const void *valB;
+    int64_t *rowptr64;
+    int32_t *rowptr32;
+    int32_t *colidxC;
+    void *valC;
+    int64_t *nnz_dev;
+    int64_t capC;
+    int32_t m, k, n, nnzA;
+    int32_t mstart, kstart, estart;  // first global row, column and A entry
+    int32_t colbits, rmax_log2, capacity, chunk, level;
+};
+
+// Per-product values found on the device.
+struct BatchProd {
+    int64_t flop;
+    unsigned long long max_light;  // largest row flop <= capacity / 2
+    unsigned long long max_row;    // largest row flop
+    int64_t first_bin;
+    int64_t chunk_base;            // first expand work item
+};
+
+struct BatchHeader {
+    int64_t nbins;
+    int64_t nchunks;
+    int64_t tuples;                // padded tuple slots used
+    int64_t level_bins[8];         // bins of capacity level l: [level_bins[l], level_bins[l+1])
+};
+
 struct NumericArgs {
     // inputs
     int32_t m, k, n;
@@ -265,11 +309,22 @@ struct NumericArgs {
     uint32_t *skeys;
     void *svals;
     int over_passes;
+    // batched products (null for a single product)
+    const BatchDesc *desc;
+    const int32_t *chunk_prod;  // [nchunks] product of each expand work item
+    const int32_t *bin_prod;    // [nbins] product of each bin
+    const BatchProd *prod;
+    const BatchHeader *bhdr;    // device-side counts: nbins, nchunks, bin range of each level
+    int32_t level;              // capacity level the sort launch serves
 };
 
 cudaError_t launch_expand(const NumericArgs &a, cudaStream_t s);
 
 cudaError_t launch_binsort(const NumericArgs &a, cudaStream_t s);
+// Batched forms: work counts are read from a.bhdr on the device; the grids are
+// persistent (sized from the SM count).
+cudaError_t launch_expand_batch(const NumericArgs &a, cudaStream_t s);
+cudaError_t launch_binsort_batch(const NumericArgs &a, cudaStream_t s);
 int binsort_max_capacity(int dtype);
 
 }  // namespace pb

@@ -53,7 +53,8 @@ struct Batch {  // one A entry per lane
 };
 
 template <class IV>
-__device__ inline Batch<IV> load_batch(const NumericArgs &p, const IV *__restrict__ valA, int32_t e, bool valid) {
+__device__ inline Batch<IV> load_batch(const NumericArgs &p, const IV *__restrict__ valA,
+                                      const int32_t *__restrict__ rowptrB, int32_t e, bool valid) {
     Batch<IV> x;
     x.info = 0;
     x.av = IV(0);
@@ -65,14 +66,17 @@ __device__ inline Batch<IV> load_batch(const NumericArgs &p, const IV *__restric
         const int64_t bin = (int64_t)(x.info >> 32);
         if (bin >= p.bin_lo && bin < p.bin_hi) {  // the entry's row belongs to this panel
             x.av = valA[e];
-            x.b0 = p.rowptrB[k];
-            x.lb = p.rowptrB[k + 1] - x.b0;
+            x.b0 = rowptrB[k];
+            x.lb = rowptrB[k + 1] - x.b0;
         }
     }
     return x;
 }
 
-template <class IV, class TV>
+// BATCH: the work items of all products of a batch, one product per item;
+// A entries are indexed in the batch's global entry space and the operand
+// arrays of the item's product are taken from its descriptor.
+template <class IV, class TV, bool BATCH>
 __global__ void __launch_bounds__(256) k_expand(const NumericArgs p) {
     const int lane = threadIdx.x & 31;
     const int64_t gwarp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -80,14 +84,31 @@ __global__ void __launch_bounds__(256) k_expand(const NumericArgs p) {
     const IV *__restrict__ valA = static_cast<const IV *>(p.valA);
     const IV *__restrict__ valB = static_cast<const IV *>(p.valB);
     const int32_t *__restrict__ colidxB = p.colidxB;
+    const int32_t *__restrict__ rowptrB = p.rowptrB;
     // reserved positions are absolute tuple indices of the whole product; the
     // buffer holds this panel's tuples from tuple_base on
     uint32_t *__restrict__ keys = p.keys - p.tuple_base;
     TV *__restrict__ vals = static_cast<TV *>(p.vals) - p.tuple_base;
+    int64_t nchunks = p.nchunks;
+    if constexpr (BATCH) {
+        if (*p.err & DEV_ERR_BATCH_FATAL) return;
+        nchunks = p.bhdr->nchunks;
+    }
 
-    for (int64_t c = gwarp; c < p.nchunks; c += nwarps) {
-        const int32_t e_begin = p.chunk_e[c], e_end = p.chunk_e[c + 1];
-        Batch<IV> cur = load_batch(p, valA, e_begin + lane, e_begin + lane < e_end);
+    for (int64_t c = gwarp; c < nchunks; c += nwarps) {
+        int32_t e_begin = p.chunk_e[c], e_end = p.chunk_e[c + 1];
+        if constexpr (BATCH) {
+            const BatchDesc &d = p.desc[p.chunk_prod[c]];
+            // global entry e of this product is its local entry e - estart
+            valA = static_cast<const IV *>(d.valA) - d.estart;
+            valB = static_cast<const IV *>(d.valB);
+            colidxB = d.colidxB;
+            rowptrB = d.rowptrB;
+            const int32_t e_last = d.estart + d.nnzA;
+            e_begin = min(e_begin, e_last);
+            e_end = min(e_end, e_last);
+        }
+        Batch<IV> cur = load_batch(p, valA, rowptrB, e_begin + lane, e_begin + lane < e_end);
         for (int32_t e0 = e_begin; e0 < e_end; e0 += 32) {
             const bool valid = e0 + lane < e_end;
             const bool is_long = cur.lb >= LONG_RUN;
@@ -96,7 +117,7 @@ __global__ void __launch_bounds__(256) k_expand(const NumericArgs p) {
             if (sl > 0) pos = reserve(p, (uint32_t)(cur.info >> 32), (uint32_t)sl);
             // software pipeline: the next batch's loads overlap this batch's reservations and writes
             const int32_t en = e0 + 32 + lane;
-            const Batch<IV> nxt = load_batch(p, valA, en, en < e_end);
+            const Batch<IV> nxt = load_batch(p, valA, rowptrB, en, en < e_end);
             // ---- short runs as one flattened stream --------------------------------
             const int32_t incl = warp_inclusive_scan(sl);
             const int32_t total = __shfl_sync(FULL, incl, 31);
@@ -157,9 +178,26 @@ cudaError_t launch_expand(const NumericArgs &a, cudaStream_t s) {
     if (blocks > need) blocks = need;
     if (blocks < 1) blocks = 1;
     switch (a.dtype) {
-        case PB_F64: k_expand<double, double><<<(unsigned)blocks, threads, 0, s>>>(a); break;
-        case PB_F32: k_expand<float, float><<<(unsigned)blocks, threads, 0, s>>>(a); break;
-        case PB_F64_F32TUPLE: k_expand<double, float><<<(unsigned)blocks, threads, 0, s>>>(a); break;
+        case PB_F64: k_expand<double, double, false><<<(unsigned)blocks, threads, 0, s>>>(a); break;
+        case PB_F32: k_expand<float, float, false><<<(unsigned)blocks, threads, 0, s>>>(a); break;
+        case PB_F64_F32TUPLE: k_expand<double, float, false><<<(unsigned)blocks, threads, 0, s>>>(a); break;
+        default: return cudaErrorInvalidValue;
+    }
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+// a.nchunks is an upper bound on the work items (it only sizes the grid).
+cudaError_t launch_expand_batch(const NumericArgs &a, cudaStream_t s) {
+    const int threads = 256;
+    int64_t blocks = (int64_t)a.num_sms * 8;
+    const int64_t need = ceil_div<int64_t>(a.nchunks * 32, threads);
+    if (blocks > need) blocks = need;
+    if (blocks < 1) blocks = 1;
+    switch (a.dtype) {
+        case PB_F64: k_expand<double, double, true><<<(unsigned)blocks, threads, 0, s>>>(a); break;
+        case PB_F32: k_expand<float, float, true><<<(unsigned)blocks, threads, 0, s>>>(a); break;
+        case PB_F64_F32TUPLE: k_expand<double, float, true><<<(unsigned)blocks, threads, 0, s>>>(a); break;
         default: return cudaErrorInvalidValue;
     }
     count_launches(1);
