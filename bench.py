@@ -12,7 +12,7 @@ Printed: one JSON line (rank 0).  `value` is whole-job GFLOPS counting
 2 x multiplications; the `roofline` object reports the dominant kernel's
 algorithmic GB/s against the measured HBM copy bandwidth.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload er21|er12|er22]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload er21|er12|er22|batch1024|...]
 
 With N > 1 (torchrun) every rank runs an independent replica (the path does
 not shard onto several GPUs here); value = all ranks' flops / max rank time.
@@ -48,11 +48,18 @@ WORKLOADS = {
                  desc="ER C=A*A, n=2^19, d=8 per column, FP64 values U(-1,1), int32 indices"),
     "er12": dict(kind="er", n=4096, d=4, seed=0, dtype="f64",
                  desc="ER C=A*A, n=4096, d=4 per column, FP64 values U(-1,1), int32 indices"),
+    "batch1024": dict(kind="batch", count=1024, seed=3, dtype="f64",
+                      desc="1024 independent ER products A_i*A_i, n_i log-uniform in [512, 65536], d_i uniform "
+                           "in {2..16}, FP64, one pb_spgemm_batch call per step replayed as a CUDA graph, "
+                           "parameters autotuned per (n, d) class"),
 }
 
 
 def make_inputs(w):
     import synth
+    if w["kind"] == "batch":
+        shapes = synth.batch_er_shapes(w["count"], seed=w["seed"])
+        return [synth.er(n, d, seed=1000 * w["seed"] + i) for i, (n, d) in enumerate(shapes)]
     if w["kind"] == "rmat":
         return synth.rmat(w["scale"], w["ef"], seed=w["seed"])
     return synth.er(w["n"], w["d"], seed=w["seed"])
@@ -171,6 +178,8 @@ def run_reference(args, w):
     if rank != 0:
         return
     import oracle
+    if w["kind"] == "batch":
+        return run_reference_batch(args, w)
     A, B = make_inputs(w)
     # Each step is a bounded sample: a contiguous block of rows sized so the
     # whole run (warm-up + timed steps) stays near two minutes of CPU time.
@@ -194,6 +203,240 @@ def run_reference(args, w):
         "e2e": {"value": value, "unit": "GFLOPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+def batch_oracle_sample(probs, budget_s: float):
+    """Leading products of a batch whose oracle products take about budget_s seconds."""
+    import oracle
+    t0 = time.perf_counter()
+    n, flop = 0, 0
+    while n < len(probs) and (time.perf_counter() - t0 < budget_s or n == 0):
+        oracle.spgemm(*probs[n])
+        flop += oracle.flop(*probs[n])
+        n += 1
+    return n, flop
+
+
+def run_reference_batch(args, w):
+    import oracle
+    probs = make_inputs(w)
+    n, flop = batch_oracle_sample(probs, 120.0 / (args.steps + args.warmup))
+    for _ in range(args.warmup):
+        for A, B in probs[:n]:
+            oracle.spgemm(A, B)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        for A, B in probs[:n]:
+            oracle.spgemm(A, B)
+    dt = time.perf_counter() - t0
+    value = 2.0 * flop * args.steps / dt / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "GFLOPS", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": w["desc"], "flop": flop},
+        "cpu_baseline": {"value": value, "unit": "GFLOPS", "cores": oracle.threads(), "kind": "oracle",
+                         "sample": f"products 0..{n - 1} of {len(probs)} ({flop} multiplications) per step, "
+                                   f"{args.steps} timed steps"},
+        "e2e": {"value": value, "unit": "GFLOPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours_batch(args, w):
+    """Batched workload: one pb_spgemm_batch call (symbolic + numeric of every product) per step."""
+    import torch
+    import torch.distributed as dist
+
+    from paper_2002_11302_gb300 import binding, model
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    probs = make_inputs(w)
+    # inputs as views of six concatenated buffers (so the end-to-end run copies them in six transfers)
+    pin = lambda parts, dt: torch.from_numpy(np.concatenate([np.asarray(x, dtype=dt) for x in parts])).pin_memory()  # noqa: E731
+    fields = [("colptr", np.int32, 0), ("rowidx", np.int32, 0), ("val", np.float64, 0),
+              ("rowptr", np.int32, 1), ("colidx", np.int32, 1), ("val", np.float64, 1)]
+    host = [pin([getattr(pr[side], f) for pr in probs], dt) for f, dt, side in fields]
+    dev = [h.to("cuda") for h in host]
+    views = [[] for _ in fields]
+    for j, (f, dt, side) in enumerate(fields):
+        off = 0
+        for pr in probs:
+            n = getattr(pr[side], f).shape[0]
+            views[j].append(dev[j][off:off + n])
+            off += n
+    As = [binding.CscMatrix(A.nrows, A.ncols, views[0][i], views[1][i], views[2][i]) for i, (A, _) in enumerate(probs)]
+    Bs = [binding.CsrMatrix(B.nrows, B.ncols, views[3][i], views[4][i], views[5][i]) for i, (_, B) in enumerate(probs)]
+    handle = binding.Handle()
+    bt = binding.Batch(As, Bs, handle=handle)
+    flop = int(bt.flop.sum())
+    tune_s = None
+    if not args.no_tune:
+        t0 = time.perf_counter()
+        bt.autotune(reps=2)
+        tune_s = time.perf_counter() - t0
+    stream = torch.cuda.Stream()
+    stream.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(stream):
+        l0 = binding.kernel_launches()
+        bt.run(stream=stream)
+        launches_per_call = binding.kernel_launches() - l0
+    torch.cuda.synchronize()
+    if bt.status() != 0:
+        raise RuntimeError(f"device status {bt.status()} in the batch warm-up")
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=stream):
+        bt.run(stream=stream)
+    for _ in range(args.warmup):
+        graph.replay()
+    torch.cuda.synchronize()
+    if bt.status() != 0:
+        raise RuntimeError(f"device status {bt.status()} in the graph warm-up")
+    nnz = bt.nnz.cpu().numpy()
+
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
+    time.sleep(0.2)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        t_start.record(stream)
+        for _ in range(args.steps):
+            graph.replay()
+        t_end.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = sampler.stop()
+    total_ms = t_start.elapsed_time(t_end)
+    if bt.status() != 0:
+        raise RuntimeError(f"device status {bt.status()} in the timed region")
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = 2.0 * flop * args.steps * world / (total_ms / 1e3) / 1e9
+
+    # per-phase kernel times (plain launches with phase events, after the timed region)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    binding.set_phase_events(handle, ev)
+    ph = {"symbolic": 0.0, "expand": 0.0, "sort_compress": 0.0}
+    reps = 5
+    with torch.cuda.stream(stream):
+        for _ in range(reps):
+            bt.run(stream=stream)
+            ev[3].synchronize()
+            ph["symbolic"] += ev[0].elapsed_time(ev[1]) / reps
+            ph["expand"] += ev[1].elapsed_time(ev[2]) / reps
+            ph["sort_compress"] += ev[2].elapsed_time(ev[3]) / reps
+    binding.set_phase_events(handle, None)
+    by = [model.bytes_alg(A.nrows, A.ncols, A.nnz, B.nnz, int(bt.flop[i]), int(nnz[i]), val_in=8, tuple_bytes=12,
+                          val_out=8, rowptr_out=8) for i, (A, B) in enumerate(probs)]
+    tot = {k: sum(getattr(b, k) for b in by) for k in ("expand", "sort", "compress", "numeric", "total")}
+    hbm, peak_kind = measured_peaks()
+    kern = {"expand": (tot["expand"], ph["expand"], "k_expand"),
+            "sort_compress": (tot["sort"] + tot["compress"], ph["sort_compress"], "k_binsort")}
+    dom = max(kern, key=lambda k: kern[k][1])
+    bytes_dom, ms_dom, kname = kern[dom]
+    achieved = bytes_dom / (ms_dom / 1e3) / 1e9
+    numeric_ms = ph["expand"] + ph["sort_compress"]
+
+    # the same products, one plain call each (symbolic + allocation + numeric per product)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for A, B in zip(As, Bs):
+        binding.spgemm(A, B, handle=handle)
+    torch.cuda.synchronize()
+    plain_ms = (time.perf_counter() - t0) * 1e3
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "GFLOPS", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w["desc"], "count": len(probs), "rows": int(sum(A.nrows for A, _ in probs)),
+                   "nnz_a": int(sum(A.nnz for A, _ in probs)), "flop": flop, "nnz_c": int(nnz.sum()),
+                   "tuple_bytes": 12, "autotune_s": tune_s, "tuning_classes": len(binding.get_tuning(handle)),
+                   "l2": "no flush: the inputs and the tuple buffer each exceed the 129 MB L2",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "roofline": {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": achieved / hbm, "peak_kind": peak_kind, "traffic": None,
+                     "alg_bytes_per_launch": bytes_dom, "ms_per_launch": ms_dom},
+        "pct_beta_ai": {"numeric": tot["numeric"] / (numeric_ms / 1e3) / 1e9 / hbm,
+                        "step": tot["total"] / (ms_per_step / 1e3) / 1e9 / hbm, "beta_gbs": hbm,
+                        "beta_kind": peak_kind},
+        "phases_ms": ph,
+        "vs_plain_per_call": {"plain_ms": plain_ms, "plain_gflops": 2.0 * flop / (plain_ms / 1e3) / 1e9,
+                              "speedup": plain_ms / ms_per_step},
+        "gpu_launches": launches_per_call * args.steps,
+        "clocks": clocks,
+    }
+    if not args.no_e2e:
+        line["e2e"] = run_e2e_batch(args, probs, host, dev, bt, stream, torch)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        n, sflop = batch_oracle_sample(probs, 8.0)
+        t0 = time.perf_counter()
+        for A, B in probs[:n]:
+            oracle.spgemm(A, B)
+        t = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": 2.0 * sflop / t / 1e9, "unit": "GFLOPS", "cores": oracle.threads(),
+                                "kind": "oracle", "sample": f"products 0..{n - 1} of {len(probs)} "
+                                                            f"({sflop} of {flop} multiplications)"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def run_e2e_batch(args, probs, host, dev, bt, stream, torch):
+    """The batch through the public API with host buffers: H2D of all inputs and D2H of every C per step."""
+    n = len(probs)
+    hrow = [torch.empty(C.rowptr.numel(), dtype=torch.int64).pin_memory() for C in bt.C]
+    hcol = [torch.empty(C.colidx.numel(), dtype=torch.int32).pin_memory() for C in bt.C]
+    hval = [torch.empty(C.val.numel(), dtype=torch.float64).pin_memory() for C in bt.C]
+    hnnz = torch.empty(n, dtype=torch.int64).pin_memory()
+    h2d = sum(t.numel() * t.element_size() for t in host)
+
+    def one():
+        with torch.cuda.stream(stream):
+            for d, h in zip(dev, host):
+                d.copy_(h, non_blocking=True)
+            bt.run(stream=stream)
+            hnnz.copy_(bt.nnz[:n], non_blocking=True)
+            for i, C in enumerate(bt.C):
+                hrow[i].copy_(C.rowptr, non_blocking=True)
+            stream.synchronize()
+            d2h = 8 * n
+            for i, C in enumerate(bt.C):
+                k = int(hnnz[i])
+                hcol[i][:k].copy_(C.colidx[:k], non_blocking=True)
+                hval[i][:k].copy_(C.val[:k], non_blocking=True)
+                d2h += 8 * C.rowptr.numel() + 12 * k
+            return d2h
+
+    for _ in range(3):
+        one()
+    torch.cuda.synchronize()
+    steps = max(args.steps // 10, 3)
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s.record(stream)
+    for _ in range(steps):
+        d2h = one()
+    e.record(stream)
+    torch.cuda.synchronize()
+    ms = s.elapsed_time(e) / steps
+    flop = int(bt.flop.sum())
+    return {"value": 2.0 * flop / (ms / 1e3) / 1e9, "unit": "GFLOPS", "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": d2h, "ms_per_step": ms, "steps": steps}
 
 
 def run_ours(args, w):
@@ -388,11 +631,14 @@ def main():
     ap.add_argument("--chunk", type=int, default=0, help="tuples per expand work item (0 = default)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-tune", action="store_true", help="batch workload: skip the autotuner")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     w = WORKLOADS[args.workload]
     if args.impl == "reference":
         run_reference(args, w)
+    elif w["kind"] == "batch":
+        run_ours_batch(args, w)
     else:
         run_ours(args, w)
 

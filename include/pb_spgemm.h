@@ -186,7 +186,10 @@ pb_status pb_plan_destroy(pb_plan *plan);
  * this handle records events[0] before its first launch, events[1] after the
  * workspace reset, events[2] after the expand kernel and events[3] after the
  * sort/compress kernel, on the call's stream.  The four entries are cudaEvent_t
- * handles owned by the caller; NULL disables recording.
+ * handles owned by the caller; NULL disables recording.  pb_spgemm_batch
+ * records events[0] before its first launch, events[1] after its symbolic
+ * kernels, events[2] after the expand kernel and events[3] after the last
+ * sort launch (when the batch is not empty).
  * pb_kernel_launches: number of CUDA kernels this library has launched in the
  * process so far (all handles). */
 pb_status pb_set_phase_events(pb_handle *h, void *const *events);

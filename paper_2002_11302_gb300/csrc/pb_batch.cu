@@ -673,6 +673,7 @@ pb_status launch_batch(pb_handle *h, const BatchHost &bh, const BatchWs &w, pb_d
                        int32_t *device_status) {
     const int32_t count = bh.count;
     const int64_t cap = (int64_t)h->num_sms * 16;
+    if (h->phase_on) PB_CUDA_H(h, cudaEventRecord(h->phase_ev[0], s));
     pb_status st = launch_front(h, bh, w, s);
     if (st != PB_OK) return st;
     if (count > 0) {
@@ -720,7 +721,9 @@ pb_status launch_batch(pb_handle *h, const BatchHost &bh, const BatchWs &w, pb_d
         a.bin_prod = w.bin_prod;
         a.prod = w.prod;
         a.bhdr = w.bhdr;
+        if (h->phase_on) PB_CUDA_H(h, cudaEventRecord(h->phase_ev[1], s));
         PB_CUDA_H(h, launch_expand_batch(a, s));
+        if (h->phase_on) PB_CUDA_H(h, cudaEventRecord(h->phase_ev[2], s));
         for (int l = 0; l < NLEVELS; ++l) {
             if (bh.level_rows[l] == 0) continue;
             a.capacity = kLevelCap[l];
@@ -730,6 +733,7 @@ pb_status launch_batch(pb_handle *h, const BatchHost &bh, const BatchWs &w, pb_d
             a.bin_hi = bh.level_rows[l];  // bound on the level's bins: sizes the grid
             PB_CUDA_H(h, launch_binsort_batch(a, s));
         }
+        if (h->phase_on) PB_CUDA_H(h, cudaEventRecord(h->phase_ev[3], s));
     }
     k_bfinish<<<1, 1, 0, s>>>(w.err, device_status);
     count_launches(1);
