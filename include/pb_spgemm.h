@@ -277,6 +277,70 @@ pb_status pb_batch_get_tuning(const pb_handle *h, pb_batch_tune *out, int32_t ca
 pb_status pb_batch_set_tuning(pb_handle *h, const pb_batch_tune *entries, int32_t n);
 
 /*
+ * Serving: a request loop with continuous batching (no counterpart in the
+ * paper; each request runs the paper's method through the entry points above).
+ *
+ * A server owns `max_slots` CUDA streams and one worker thread.  Requests are
+ * admitted in arrival order as soon as a slot is free and the device memory the
+ * request needs fits the HBM budget; admitted requests run concurrently on
+ * their slots' streams, so a request arriving while others are on the GPU
+ * starts without waiting for them.  Operands stay where the caller put them
+ * (device memory, kept alive until the request is done); the server allocates
+ * plans, workspaces, intermediates and results itself with cudaMallocAsync on
+ * the slot's stream (not through the handle's allocator) and counts every byte
+ * against the budget.  Results stay resident, and count against the budget,
+ * until pb_serve_release.
+ *
+ * Request kinds:
+ *   PB_REQ_PRODUCT   C = A * B (A CSC, B CSR), e.g. a Markov-clustering
+ *                    squaring M * M of a column-stochastic M.
+ *   PB_REQ_GALERKIN  C = P^T (A P), the coarse operator of an AMG level:
+ *                    A (n x n, CSC) in `A`, the prolongator P (n x nc, CSR) in
+ *                    `B`.  Two products: AP = A * P (CSR), then P^T * AP with
+ *                    P^T taken as the CSC view of P's CSR arrays.
+ * A request whose need exceeds the whole budget completes with PB_ERR_BUSY.
+ * When every admitted request is waiting for memory (a Galerkin request's
+ * second product needs more than is free), the most recently admitted one is
+ * preempted: its memory is released and it is queued again at the front.
+ */
+typedef enum pb_request_kind { PB_REQ_PRODUCT = 0, PB_REQ_GALERKIN = 1 } pb_request_kind;
+
+typedef struct pb_request {
+    int32_t kind;   /* pb_request_kind */
+    int32_t dtype;  /* pb_dtype */
+    pb_csc A;
+    pb_csr B;
+} pb_request;
+
+typedef struct pb_server pb_server;
+
+/* Create a server on the handle's device.  hbm_budget: bytes the server may
+ * hold at once; max_slots: requests in flight at once (1..64). */
+pb_status pb_server_create(pb_handle *h, size_t hbm_budget, int32_t max_slots, pb_server **s);
+/* Finish every admitted and queued request, free all server memory (including
+ * unreleased results) and stop the worker. */
+pb_status pb_server_destroy(pb_server *s);
+/* Queue a request; *req_id identifies it.  Returns PB_ERR_BUSY at once when a
+ * lower bound of its need (its operands' index arrays) already exceeds the
+ * budget, and argument errors as pb_spgemm_symbolic does. */
+pb_status pb_serve_submit(pb_server *s, const pb_request *req, uint64_t *req_id);
+/* *done = 1 once the request has finished; *result is then its status. */
+pb_status pb_serve_poll(pb_server *s, uint64_t req_id, int32_t *done, pb_status *result);
+/* Block until the request has finished; *result receives its status. */
+pb_status pb_serve_wait(pb_server *s, uint64_t req_id, pb_status *result);
+/* Device pointers of a finished request's C (int64 row pointer; C->cap = nnz(C);
+ * C->nnz_dev = NULL).  Owned by the server until pb_serve_release. */
+pb_status pb_serve_result(pb_server *s, uint64_t req_id, pb_csr_out *C);
+/* Host-clock times of a finished request in milliseconds: queued (submit to
+ * admission) and total (submit to completion seen by the worker). */
+pb_status pb_serve_timing(pb_server *s, uint64_t req_id, double *queued_ms, double *total_ms);
+/* Free a finished request's result and forget the request. */
+pb_status pb_serve_release(pb_server *s, uint64_t req_id);
+/* Counters: requests completed and preempted, bytes held now and at most. */
+pb_status pb_serve_stats(pb_server *s, int64_t *completed, int64_t *preempted, size_t *bytes_in_use,
+                         size_t *peak_bytes);
+
+/*
  * No-allocation entry point (the paper has no counterpart; this serves callers).
  *
  * Some callers cannot allocate device memory where they need a product: code

@@ -63,6 +63,10 @@ class _BatchTune(ctypes.Structure):
                 ("rmax_log2", ctypes.c_int32), ("expand_chunk", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
+class _Request(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("dtype", ctypes.c_int32), ("A", _CSC), ("B", _CSR)]
+
+
 _ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
 _FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
 
@@ -97,6 +101,17 @@ SIGNATURES = {
                                          ctypes.POINTER(_CSROut), ctypes.c_int, _VP, _SZ, _VP, _I32]),
     "pb_batch_get_tuning": (ctypes.c_int, [_VP, ctypes.POINTER(_BatchTune), _I32, ctypes.POINTER(_I32)]),
     "pb_batch_set_tuning": (ctypes.c_int, [_VP, ctypes.POINTER(_BatchTune), _I32]),
+    "pb_server_create": (ctypes.c_int, [_VP, _SZ, _I32, ctypes.POINTER(_VP)]),
+    "pb_server_destroy": (ctypes.c_int, [_VP]),
+    "pb_serve_submit": (ctypes.c_int, [_VP, ctypes.POINTER(_Request), ctypes.POINTER(ctypes.c_uint64)]),
+    "pb_serve_poll": (ctypes.c_int, [_VP, ctypes.c_uint64, ctypes.POINTER(_I32), ctypes.POINTER(ctypes.c_int)]),
+    "pb_serve_wait": (ctypes.c_int, [_VP, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int)]),
+    "pb_serve_result": (ctypes.c_int, [_VP, ctypes.c_uint64, ctypes.POINTER(_CSROut)]),
+    "pb_serve_timing": (ctypes.c_int, [_VP, ctypes.c_uint64, ctypes.POINTER(ctypes.c_double),
+                                       ctypes.POINTER(ctypes.c_double)]),
+    "pb_serve_release": (ctypes.c_int, [_VP, ctypes.c_uint64]),
+    "pb_serve_stats": (ctypes.c_int, [_VP, ctypes.POINTER(_I64), ctypes.POINTER(_I64), ctypes.POINTER(_SZ),
+                                      ctypes.POINTER(_SZ)]),
 }
 
 _lib = None
@@ -496,3 +511,100 @@ def set_tuning(entries, handle: Optional[Handle] = None) -> None:
         *[_BatchTune(e["log2n"], e["dclass"], e["bin_capacity"], e["rmax_log2"], e["expand_chunk"], 0)
           for e in entries])
     _check(h.lib, h.ptr, h.lib.pb_batch_set_tuning(h.ptr, arr, len(entries)))
+
+
+# ---------------------------------------------------------------------------
+# Serving (pb_server_*): continuous batching of product and Galerkin requests.
+# ---------------------------------------------------------------------------
+PB_REQ_PRODUCT = 0
+PB_REQ_GALERKIN = 1
+
+
+class _DevView:
+    """A device array the server owns, exposed to torch without a copy."""
+
+    def __init__(self, ptr: int, n: int, typestr: str):
+        self.__cuda_array_interface__ = {"shape": (n,), "typestr": typestr, "data": (ptr, False), "version": 3}
+
+
+def _view(ptr, n, dtype):
+    if n == 0 or not ptr:
+        return torch.empty(0, dtype=dtype, device="cuda")
+    typestr = {torch.int64: "<i8", torch.int32: "<i4", torch.float64: "<f8", torch.float32: "<f4"}[dtype]
+    return torch.as_tensor(_DevView(int(ptr), int(n), typestr), device="cuda")
+
+
+class Server:
+    """pb_server: requests are admitted as slots and HBM budget free up and overlap on the GPU."""
+
+    def __init__(self, budget_bytes: int, max_slots: int = 4, handle: Optional[Handle] = None):
+        self.handle = handle or default_handle()
+        self.lib = self.handle.lib
+        s = ctypes.c_void_p()
+        _check(self.lib, self.handle.ptr, self.lib.pb_server_create(self.handle.ptr, budget_bytes, max_slots,
+                                                                     ctypes.byref(s)))
+        self.ptr = s
+        self._keep = {}  # request id -> operands kept alive until release
+
+    def _submit(self, kind, A: CscMatrix, B: CsrMatrix, dtype: int) -> int:
+        req = _Request(kind, dtype, A._c(), B._c())
+        rid = ctypes.c_uint64()
+        _check(self.lib, self.handle.ptr, self.lib.pb_serve_submit(self.ptr, ctypes.byref(req), ctypes.byref(rid)))
+        self._keep[rid.value] = (A, B, dtype, kind)
+        return rid.value
+
+    def submit_product(self, A: CscMatrix, B: CsrMatrix, dtype: int = PB_F64) -> int:
+        """C = A * B."""
+        return self._submit(PB_REQ_PRODUCT, A, B, dtype)
+
+    def submit_galerkin(self, A: CscMatrix, P: CsrMatrix, dtype: int = PB_F64) -> int:
+        """C = P^T (A P)."""
+        return self._submit(PB_REQ_GALERKIN, A, P, dtype)
+
+    def poll(self, rid: int):
+        done, st = _I32(), ctypes.c_int()
+        _check(self.lib, self.handle.ptr, self.lib.pb_serve_poll(self.ptr, rid, ctypes.byref(done), ctypes.byref(st)))
+        return bool(done.value), int(st.value)
+
+    def wait(self, rid: int) -> int:
+        st = ctypes.c_int()
+        _check(self.lib, self.handle.ptr, self.lib.pb_serve_wait(self.ptr, rid, ctypes.byref(st)))
+        return int(st.value)
+
+    def result(self, rid: int, copy: bool = True) -> CsrMatrix:
+        """The finished request's C (cloned into torch memory unless copy=False)."""
+        C = _CSROut()
+        _check(self.lib, self.handle.ptr, self.lib.pb_serve_result(self.ptr, rid, ctypes.byref(C)))
+        dtype = self._keep[rid][2]
+        vt = _OUT_DTYPE[dtype]
+        rp = _view(C.rowptr64, C.nrows + 1, torch.int64)
+        ci = _view(C.colidx, C.cap, torch.int32)
+        va = _view(C.val, C.cap, vt)
+        if copy:
+            rp, ci, va = rp.clone(), ci.clone(), va.clone()
+        return CsrMatrix(C.nrows, C.ncols, rp, ci, va)
+
+    def timing(self, rid: int):
+        """(queued_ms, total_ms) of a finished request."""
+        q, t = ctypes.c_double(), ctypes.c_double()
+        _check(self.lib, self.handle.ptr, self.lib.pb_serve_timing(self.ptr, rid, ctypes.byref(q), ctypes.byref(t)))
+        return q.value, t.value
+
+    def release(self, rid: int) -> None:
+        _check(self.lib, self.handle.ptr, self.lib.pb_serve_release(self.ptr, rid))
+        self._keep.pop(rid, None)
+
+    def stats(self) -> dict:
+        c, p, u, k = _I64(), _I64(), _SZ(), _SZ()
+        _check(self.lib, self.handle.ptr, self.lib.pb_serve_stats(self.ptr, ctypes.byref(c), ctypes.byref(p),
+                                                                  ctypes.byref(u), ctypes.byref(k)))
+        return {"completed": c.value, "preempted": p.value, "bytes_in_use": u.value, "peak_bytes": k.value}
+
+    def close(self) -> None:
+        if getattr(self, "ptr", None):
+            self.lib.pb_server_destroy(self.ptr)
+            self.ptr = None
+            self._keep.clear()
+
+    def __del__(self):
+        self.close()

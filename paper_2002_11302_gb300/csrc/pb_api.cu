@@ -129,6 +129,7 @@ namespace pb {
 pb_status host_fail(pb_handle *h, pb_status st, const std::string &msg) { return fail(h, st, msg); }
 pb_status host_cuda_fail(pb_handle *h, cudaError_t e, const char *where) { return cuda_fail(h, e, where); }
 pb_status host_check_operands(pb_handle *h, const pb_csc *A, const pb_csr *B) { return check_operands(h, A, B); }
+size_t plan_device_bytes(const pb_plan *p) { return p ? p->arena_bytes + p->chunk_bytes + p->over_map_bytes : 0; }
 }  // namespace pb
 
 extern "C" {

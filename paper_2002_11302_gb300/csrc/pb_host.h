@@ -25,6 +25,8 @@ namespace pb {
 pb_status host_fail(pb_handle *h, pb_status st, const std::string &msg);
 pb_status host_cuda_fail(pb_handle *h, cudaError_t e, const char *where);
 pb_status host_check_operands(pb_handle *h, const pb_csc *A, const pb_csr *B);
+// Device bytes a plan holds (its arena, work-item table and oversize map).
+size_t plan_device_bytes(const pb_plan *p);
 
 }  // namespace pb
 
