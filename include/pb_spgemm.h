@@ -280,11 +280,15 @@ pb_status pb_batch_set_tuning(pb_handle *h, const pb_batch_tune *entries, int32_
  * Serving: a request loop with continuous batching (no counterpart in the
  * paper; each request runs the paper's method through the entry points above).
  *
- * A server owns `max_slots` CUDA streams and one worker thread.  Requests are
- * admitted in arrival order as soon as a slot is free and the device memory the
- * request needs fits the HBM budget; admitted requests run concurrently on
- * their slots' streams, so a request arriving while others are on the GPU
- * starts without waiting for them.  Operands stay where the caller put them
+ * A server owns `max_slots` slots, each a host thread with its own CUDA
+ * stream.  A free slot admits a queued request as soon as the device memory it
+ * needs fits the HBM budget; admitted requests run concurrently on their
+ * slots' streams, so a request arriving while others are on the GPU starts
+ * without waiting for them.  Among queued requests the one with the least
+ * estimated work (nnz(A) times the mean row length of B) is admitted first,
+ * unless the oldest queued request has already been passed over 16 times.
+ * A product whose flop-sized C could never fit the budget is sized exactly by
+ * a counting run first.  Operands stay where the caller put them
  * (device memory, kept alive until the request is done); the server allocates
  * plans, workspaces, intermediates and results itself with cudaMallocAsync on
  * the slot's stream (not through the handle's allocator) and counts every byte
@@ -299,8 +303,8 @@ pb_status pb_batch_set_tuning(pb_handle *h, const pb_batch_tune *entries, int32_
  *                    `B`.  Two products: AP = A * P (CSR), then P^T * AP with
  *                    P^T taken as the CSC view of P's CSR arrays.
  * A request whose need exceeds the whole budget completes with PB_ERR_BUSY.
- * When every admitted request is waiting for memory (a Galerkin request's
- * second product needs more than is free), the most recently admitted one is
+ * No request is admitted while an admitted one waits for memory.  When every
+ * admitted request is waiting for memory, the most recently admitted one is
  * preempted: its memory is released and it is queued again at the front.
  */
 typedef enum pb_request_kind { PB_REQ_PRODUCT = 0, PB_REQ_GALERKIN = 1 } pb_request_kind;

@@ -1,18 +1,23 @@
 // Serving loop with continuous batching over the PB-SpGEMM entry points.
 //
-// One worker thread drives `max_slots` CUDA streams.  A request is a short
-// chain of products (one for C = A*B, two for the Galerkin product P^T (A P)),
-// each run as: symbolic phase (Alg. 3; synchronises only the slot's stream),
-// optionally a counting run (when a flop-sized C would take more than a quarter
-// of the budget), then the numeric phase (Alg. 2).  The worker admits queued
-// requests in arrival order while a slot is free and their memory fits the
-// budget, and advances every admitted request when its stream's event fires, so
-// requests arriving while others run on the GPU overlap with them.
+// A server has `max_slots` slots; each slot is a host thread with its own CUDA
+// stream and library handle.  A free slot takes the oldest queued request and
+// runs it to completion: a short chain of products (one for C = A*B, two for
+// the Galerkin product P^T (A P)), each as the symbolic phase (Alg. 3; its one
+// host synchronisation blocks only this slot), optionally a counting run (when
+// a flop-sized C could never fit the budget), then the numeric phase (Alg. 2).
+// Slots run concurrently, so a request that arrives while others are on the
+// GPU starts as soon as a slot and memory are free and its kernels overlap
+// with theirs.  Among queued requests the one with the least estimated work
+// goes first (nnz(A) times the mean row length of B), unless the oldest has
+// been passed over MAX_BYPASS times already.
 //
 // Every device byte the server holds (plans, workspaces, intermediates and
 // results) comes from the server's own memory pool and is counted against the
-// budget.  When all admitted requests wait for memory, the most recently
-// admitted one is preempted (its memory released, the request queued again).
+// budget before it is allocated.  A slot that lacks memory waits; no new
+// request is admitted while any slot waits.  When every busy slot waits, the
+// most recently admitted request is preempted: its memory is released and it
+// is queued again at the front.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -38,28 +43,21 @@ struct Buf {
     size_t bytes = 0;
 };
 
-enum Phase { QUEUED, PLAN, MEM, COUNTING, RUNNING, DONE };
-
 struct Req {
     uint64_t id = 0;
     pb_request r{};
-    int step = 0, nsteps = 1;
-    Phase phase = QUEUED;
-    bool waiting = false;  // the last attempt to advance found too little memory
-    bool counted = false;  // a counting run sized this step's output exactly
+    int nsteps = 1;
+    bool done = false;
+    bool preempt = false;  // set by another slot: release everything and queue again
+    bool waiting = false;  // waiting for memory
     pb_status result = PB_OK;
-    int slot = -1;
     int restarts = 0;
     bool admitted_once = false;
+    int bypassed = 0;      // later requests admitted before this one
+    double est = 0;        // estimated work (flop)
     Clock::time_point t_submit, t_first_admit, t_admit, t_done;
-    pb_plan *plan = nullptr;
-    size_t plan_bytes = 0;   // reserved for the plan
-    int64_t flop = 0, nnz = 0;
-    Buf ws, nnz_dev;
-    Buf out_rowptr, out_colidx, out_val;  // this step's C
-    Buf prev_rowptr, prev_colidx, prev_val;  // the previous step's C (Galerkin: AP)
-    int64_t prev_nnz = 0;
-    cudaEvent_t ev = nullptr;
+    int64_t nnz = 0;
+    Buf out_rowptr, out_colidx, out_val;  // the final C
 };
 
 size_t val_bytes(int32_t dtype) { return dtype == PB_F32 ? 4 : 8; }
@@ -68,31 +66,66 @@ size_t val_bytes(int32_t dtype) { return dtype == PB_F32 ? 4 : 8; }
 
 struct pb_server {
     pb_handle *user = nullptr;
-    pb_handle *h = nullptr;  // the worker's own handle (plans come from the server pool)
     int device = 0;
     cudaMemPool_t pool = nullptr;
     size_t budget = 0, in_use = 0, peak = 0;
     int max_slots = 0;
     std::vector<cudaStream_t> streams;
-    std::vector<Req *> slots;
+    std::vector<pb_handle *> hs;  // one library handle per slot (plans come from the server pool)
+    std::vector<Req *> active;    // request running in each slot
     std::deque<Req *> queue;
     std::unordered_map<uint64_t, Req *> reqs;
-    std::vector<Buf> to_free;     // released results, freed by the worker
-    std::vector<Req *> to_delete; // released requests: only the worker deletes requests
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
-    std::thread worker;
+    std::vector<std::thread> threads;
     bool stop = false;
+    int waiting = 0;  // slots waiting for memory
     uint64_t next_id = 1;
     int64_t completed = 0, preempted = 0;
 };
 
 namespace {
 
+constexpr int MAX_BYPASS = 16;
+
+struct SlotCtx {
+    pb_server *S;
+    int slot;
+};
+
 // ---- budget -----------------------------------------------------------------
-bool reserve(pb_server *S, size_t b) {
-    std::lock_guard<std::mutex> lk(S->mu);
-    if (S->in_use + b > S->budget) return false;
+// Reserve `b` bytes, waiting while they do not fit.  Returns false when this
+// request has been chosen for preemption.
+bool wait_reserve(pb_server *S, Req *q, size_t b) {
+    std::unique_lock<std::mutex> lk(S->mu);
+    bool counted = false;
+    while (S->in_use + b > S->budget) {
+        if (q->preempt) break;
+        if (!counted) {
+            counted = true;
+            q->waiting = true;
+            ++S->waiting;
+        }
+        int busy = 0;
+        Req *youngest = nullptr;
+        for (Req *x : S->active) {
+            if (!x) continue;
+            ++busy;
+            if (x->waiting && (!youngest || x->t_admit > youngest->t_admit)) youngest = x;
+        }
+        if (busy >= 2 && S->waiting == busy && youngest) {
+            youngest->preempt = true;
+            S->cv_work.notify_all();
+            if (youngest == q) break;
+        }
+        S->cv_work.wait_for(lk, std::chrono::milliseconds(5));
+    }
+    if (counted) {
+        q->waiting = false;
+        --S->waiting;
+        S->cv_work.notify_all();
+    }
+    if (q->preempt) return false;
     S->in_use += b;
     S->peak = std::max(S->peak, S->in_use);
     return true;
@@ -107,24 +140,28 @@ void force_reserve(pb_server *S, size_t b) {
 void unreserve(pb_server *S, size_t b) {
     std::lock_guard<std::mutex> lk(S->mu);
     S->in_use -= std::min(b, S->in_use);
+    S->cv_work.notify_all();
 }
 
-cudaStream_t stream_of(pb_server *S, const Req *q) { return S->streams[q->slot >= 0 ? q->slot : 0]; }
-
-// Reserve and allocate; false when the budget has no room (nothing allocated).
-bool get(pb_server *S, Req *q, Buf &b, size_t bytes, pb_status *err) {
-    bytes = std::max<size_t>(bytes, 256);
-    if (!reserve(S, bytes)) return false;
+// Allocate bytes already reserved; on success they move from *left to b.
+pb_status alloc(pb_server *S, cudaStream_t s, Buf &b, size_t bytes, size_t *left) {
     void *p = nullptr;
-    if (cudaMallocFromPoolAsync(&p, bytes, S->pool, stream_of(S, q)) != cudaSuccess) {
+    if (cudaMallocFromPoolAsync(&p, bytes, S->pool, s) != cudaSuccess) {
         (void)cudaGetLastError();
-        unreserve(S, bytes);
-        *err = PB_ERR_OOM;
-        return true;
+        return PB_ERR_OOM;
     }
     b.p = p;
     b.bytes = bytes;
-    return true;
+    *left -= bytes;
+    return PB_OK;
+}
+
+// nnz(C) written by the step's kernels, read on the slot's stream.
+pb_status read_nnz(cudaStream_t s, const Buf &nnz, int64_t *out) {
+    if (cudaMemcpyAsync(out, nnz.p, 8, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return PB_ERR_CUDA;
+    return PB_OK;
 }
 
 void put(pb_server *S, cudaStream_t s, Buf &b) {
@@ -134,9 +171,10 @@ void put(pb_server *S, cudaStream_t s, Buf &b) {
     b = Buf{};
 }
 
-// Allocator of the worker's handle: plan arrays from the server pool.  Plans
-// are only destroyed after their stream's work has completed, so freeing on
-// the first server stream is safe.
+size_t r256(size_t b) { return std::max<size_t>((b + 255) & ~size_t(255), 256); }
+
+// Allocator of the slots' handles: plan arrays from the server pool (counted
+// by the caller through plan_device_bytes).
 void *pool_alloc(size_t bytes, pb_stream_t stream, void *ctx) {
     pb_server *S = static_cast<pb_server *>(ctx);
     void *p = nullptr;
@@ -148,335 +186,210 @@ void *pool_alloc(size_t bytes, pb_stream_t stream, void *ctx) {
     return p;
 }
 
+// Plans are destroyed only after their stream has finished with them.
 void pool_free(void *p, size_t, pb_stream_t stream, void *ctx) {
     pb_server *S = static_cast<pb_server *>(ctx);
     if (p) (void)cudaFreeAsync(p, stream ? reinterpret_cast<cudaStream_t>(stream) : S->streams[0]);
 }
 
-// ---- one product step ----------------------------------------------------------
-struct Operands {
-    pb_csc A;
-    pb_csr B;
-    bool intermediate;  // output feeds the next step (int32 row pointer)
-};
-
-Operands operands(const Req *q) {
-    const pb_request &r = q->r;
-    if (r.kind == PB_REQ_PRODUCT) return {r.A, r.B, false};
-    if (q->step == 0) return {r.A, r.B, true};  // AP = A * P
-    // P^T as CSC is P's CSR arrays read column-wise; AP is the previous step's C
-    pb_csc Pt{r.B.ncols, r.B.nrows, r.B.nnz, r.B.rowptr, r.B.colidx, r.B.val};
-    pb_csr AP{r.A.nrows, r.B.ncols, q->prev_nnz, static_cast<const int32_t *>(q->prev_rowptr.p),
-              static_cast<const int32_t *>(q->prev_colidx.p), q->prev_val.p};
-    return {Pt, AP, false};
-}
-
 // Upper estimate of a plan's device bytes, reserved while the plan is built.
-size_t plan_estimate(const Operands &o) {
-    const size_t m = (size_t)o.A.nrows, k = (size_t)o.A.ncols, e = (size_t)o.A.nnz;
+size_t plan_estimate(const pb_csc &A) {
+    const size_t m = (size_t)A.nrows, k = (size_t)A.ncols, e = (size_t)A.nnz;
     return 16 * (k + 2) + 96 * (m + 2) + 12 * e + (1u << 20);
 }
 
-void release_step(pb_server *S, Req *q) {
-    cudaStream_t s = stream_of(S, q);
-    put(S, s, q->ws);
-    put(S, s, q->nnz_dev);
-    if (q->plan) {
-        pb_plan_destroy(q->plan);
-        q->plan = nullptr;
-    }
-    unreserve(S, q->plan_bytes);
-    q->plan_bytes = 0;
-}
-
-void release_all(pb_server *S, Req *q) {
-    cudaStream_t s = stream_of(S, q);
-    release_step(S, q);
-    put(S, s, q->out_rowptr);
-    put(S, s, q->out_colidx);
-    put(S, s, q->out_val);
-    put(S, s, q->prev_rowptr);
-    put(S, s, q->prev_colidx);
-    put(S, s, q->prev_val);
-}
-
 void finish(pb_server *S, Req *q, pb_status st) {
-    q->result = st;
-    if (st != PB_OK) {
-        release_all(S, q);
-    } else {
-        release_step(S, q);
-        cudaStream_t s = stream_of(S, q);
-        put(S, s, q->prev_rowptr);
-        put(S, s, q->prev_colidx);
-        put(S, s, q->prev_val);
-    }
-    q->t_done = Clock::now();
     std::lock_guard<std::mutex> lk(S->mu);
-    q->phase = DONE;
-    q->waiting = false;
-    if (q->slot >= 0) S->slots[q->slot] = nullptr;
-    q->slot = -1;
+    q->result = st;
+    q->t_done = Clock::now();
+    q->done = true;
     ++S->completed;
     S->cv_done.notify_all();
 }
 
-// Advance a request by one action.  Returns false when it must wait for memory.
-bool advance(pb_server *S, Req *q) {
-    cudaStream_t s = stream_of(S, q);
-    const int32_t dtype = q->r.dtype;
+// Everything one request holds while it runs in a slot.
+struct Held {
+    pb_plan *plan = nullptr;
+    size_t plan_bytes = 0;
+    Buf ws, nnz, prev_rowptr, prev_colidx, prev_val, out_rowptr, out_colidx, out_val;
+    int64_t prev_nnz = 0;
+};
+
+void drop_step(pb_server *S, cudaStream_t s, Held &h) {
+    put(S, s, h.ws);
+    put(S, s, h.nnz);
+    if (h.plan) pb_plan_destroy(h.plan);
+    h.plan = nullptr;
+    unreserve(S, h.plan_bytes);
+    h.plan_bytes = 0;
+}
+
+void drop_all(pb_server *S, cudaStream_t s, Held &h) {
+    drop_step(S, s, h);
+    for (Buf *b : {&h.prev_rowptr, &h.prev_colidx, &h.prev_val, &h.out_rowptr, &h.out_colidx, &h.out_val})
+        put(S, s, *b);
+}
+
+enum Outcome { OK_DONE, FAILED, PREEMPTED };
+
+// Run request q in a slot.  On success the final C stays reserved and owned by q.
+Outcome run(pb_server *S, int slot, Req *q, pb_status *status) {
+    pb_handle *hd = S->hs[slot];
+    cudaStream_t s = S->streams[slot];
+    pb_stream_t ps = reinterpret_cast<pb_stream_t>(s);
+    const pb_request &r = q->r;
+    const int32_t dtype = r.dtype;
     const size_t vb = val_bytes(dtype);
-    pb_status err = PB_OK;
-    for (;;) {
-        switch (q->phase) {
-            case PLAN: {
-                const Operands o = operands(q);
-                const size_t est = plan_estimate(o);
-                if (est > S->budget) {
-                    finish(S, q, PB_ERR_BUSY);
-                    return true;
-                }
-                if (!reserve(S, est)) return false;
-                pb_config cfg{};
-                cfg.max_tuple_bytes = (int64_t)(S->budget / 4);  // larger products run in row panels
-                pb_status st = pb_spgemm_symbolic(S->h, &o.A, &o.B, (pb_dtype)dtype, &cfg,
-                                                  reinterpret_cast<pb_stream_t>(s), &q->plan);
-                unreserve(S, est);
-                if (st != PB_OK) {
-                    q->plan = nullptr;
-                    finish(S, q, st);
-                    return true;
-                }
-                q->plan_bytes = plan_device_bytes(q->plan);
-                force_reserve(S, q->plan_bytes);
-                pb_plan_query(q->plan, &q->flop, nullptr, nullptr, nullptr, nullptr);
-                q->counted = false;
-                q->phase = MEM;
-                break;
-            }
-            case MEM: {
-                size_t ws_bytes = 0;
-                pb_plan_query(q->plan, nullptr, nullptr, &ws_bytes, nullptr, nullptr);
-                const Operands o = operands(q);
-                const size_t m = (size_t)o.A.nrows;
-                const size_t rp = o.intermediate ? 4 : 8;
-                const int64_t cap = q->counted ? q->nnz : q->flop;
-                const size_t out_bytes = rp * (m + 1) + (size_t)std::max<int64_t>(cap, 1) * (4 + vb);
-                const size_t held_other = q->prev_rowptr.bytes + q->prev_colidx.bytes + q->prev_val.bytes;
-                if (!q->counted && out_bytes > S->budget / 4) {
-                    // size C exactly first: a counting run needs only the workspace
-                    if (q->plan_bytes + held_other + ws_bytes + 256 > S->budget) {
-                        finish(S, q, PB_ERR_BUSY);
-                        return true;
-                    }
-                    if (!q->ws.p && !get(S, q, q->ws, ws_bytes, &err)) return false;
-                    if (!q->nnz_dev.p && err == PB_OK && !get(S, q, q->nnz_dev, 8, &err)) return false;
-                    if (err != PB_OK) {
-                        finish(S, q, err);
-                        return true;
-                    }
-                    pb_csr_out C{o.A.nrows, o.B.ncols, 0, nullptr, nullptr, nullptr, nullptr,
-                                 static_cast<int64_t *>(q->nnz_dev.p)};
-                    pb_status st = pb_spgemm_numeric(S->h, q->plan, &o.A, &o.B, &C, q->ws.p, q->ws.bytes,
-                                                     reinterpret_cast<pb_stream_t>(s));
-                    if (st == PB_OK && cudaEventRecord(q->ev, s) != cudaSuccess) st = PB_ERR_CUDA;
-                    if (st != PB_OK) {
-                        finish(S, q, st);
-                        return true;
-                    }
-                    q->phase = COUNTING;
-                    return true;
-                }
-                if (q->plan_bytes + held_other + ws_bytes + out_bytes + 256 > S->budget) {
-                    finish(S, q, PB_ERR_BUSY);
-                    return true;
-                }
-                // all or nothing: what this step still lacks must fit together
-                const size_t lack = (q->ws.p ? 0 : std::max<size_t>(ws_bytes, 256)) + (q->nnz_dev.p ? 0 : 256) +
-                                    std::max<size_t>(rp * (m + 1), 256) +
-                                    std::max<size_t>((size_t)std::max<int64_t>(cap, 1) * 4, 256) +
-                                    std::max<size_t>((size_t)std::max<int64_t>(cap, 1) * vb, 256);
-                if (!reserve(S, lack)) return false;
-                unreserve(S, lack);
-                if (!q->ws.p) get(S, q, q->ws, ws_bytes, &err);
-                if (err == PB_OK && !q->nnz_dev.p) get(S, q, q->nnz_dev, 8, &err);
-                if (err == PB_OK) get(S, q, q->out_rowptr, rp * (m + 1), &err);
-                if (err == PB_OK) get(S, q, q->out_colidx, (size_t)std::max<int64_t>(cap, 1) * 4, &err);
-                if (err == PB_OK) get(S, q, q->out_val, (size_t)std::max<int64_t>(cap, 1) * vb, &err);
-                if (err != PB_OK || !q->out_val.p) {
-                    finish(S, q, err != PB_OK ? err : PB_ERR_OOM);
-                    return true;
-                }
-                pb_csr_out C{o.A.nrows, o.B.ncols, cap,
-                             o.intermediate ? nullptr : static_cast<int64_t *>(q->out_rowptr.p),
-                             o.intermediate ? static_cast<int32_t *>(q->out_rowptr.p) : nullptr,
-                             static_cast<int32_t *>(q->out_colidx.p), q->out_val.p,
-                             static_cast<int64_t *>(q->nnz_dev.p)};
-                pb_status st = pb_spgemm_numeric(S->h, q->plan, &o.A, &o.B, &C, q->ws.p, q->ws.bytes,
-                                                 reinterpret_cast<pb_stream_t>(s));
-                if (st == PB_OK && cudaEventRecord(q->ev, s) != cudaSuccess) st = PB_ERR_CUDA;
-                if (st != PB_OK) {
-                    finish(S, q, st);
-                    return true;
-                }
-                q->phase = RUNNING;
-                return true;
-            }
-            case COUNTING:
-            case RUNNING: {
-                // the step's event has fired: read its device status and nnz(C)
-                pb_status dev = PB_OK;
-                pb_status st = pb_plan_status(q->plan, reinterpret_cast<pb_stream_t>(s), &dev);
-                int64_t nnz = 0;
-                if (st == PB_OK && cudaMemcpy(&nnz, q->nnz_dev.p, 8, cudaMemcpyDeviceToHost) != cudaSuccess)
-                    st = PB_ERR_CUDA;
-                if (st == PB_OK) st = dev;
-                if (st != PB_OK) {
-                    finish(S, q, st);
-                    return true;
-                }
-                q->nnz = nnz;
-                if (q->phase == COUNTING) {
-                    q->counted = true;
-                    q->phase = MEM;
-                    break;
-                }
-                const bool intermediate = operands(q).intermediate;
-                release_step(S, q);
-                if (intermediate) {
-                    // keep this step's C as the next step's B; drop the step before it
-                    put(S, s, q->prev_rowptr);
-                    put(S, s, q->prev_colidx);
-                    put(S, s, q->prev_val);
-                    q->prev_rowptr = q->out_rowptr;
-                    q->prev_colidx = q->out_colidx;
-                    q->prev_val = q->out_val;
-                    q->prev_nnz = nnz;
-                    q->out_rowptr = q->out_colidx = q->out_val = Buf{};
-                }
-                if (++q->step < q->nsteps) {
-                    q->phase = PLAN;
-                    break;
-                }
-                finish(S, q, PB_OK);
-                return true;
-            }
-            default:
-                return true;
+    Held h;
+    size_t left = 0;  // reserved but not yet allocated
+    auto fail = [&](pb_status st) {
+        (void)cudaStreamSynchronize(s);  // nothing launched may still use what is freed
+        unreserve(S, left);
+        left = 0;
+        drop_all(S, s, h);
+        *status = st;
+        return FAILED;
+    };
+    auto preempted = [&]() {
+        drop_all(S, s, h);
+        return PREEMPTED;
+    };
+    for (int step = 0; step < q->nsteps; ++step) {
+        // the operands of this step
+        pb_csc A = r.A;
+        pb_csr B = r.B;
+        bool intermediate = false;
+        if (r.kind == PB_REQ_GALERKIN && step == 0) {
+            intermediate = true;  // AP = A * P, the next step's B
+        } else if (r.kind == PB_REQ_GALERKIN) {
+            // P^T as CSC is P's CSR arrays read column-wise; AP is the previous step's C
+            A = pb_csc{r.B.ncols, r.B.nrows, r.B.nnz, r.B.rowptr, r.B.colidx, r.B.val};
+            B = pb_csr{r.A.nrows, r.B.ncols, h.prev_nnz, static_cast<const int32_t *>(h.prev_rowptr.p),
+                       static_cast<const int32_t *>(h.prev_colidx.p), h.prev_val.p};
+        }
+        const size_t held_prev = h.prev_rowptr.bytes + h.prev_colidx.bytes + h.prev_val.bytes;
+        // symbolic phase
+        const size_t est = plan_estimate(A);
+        if (est + held_prev > S->budget) return fail(PB_ERR_BUSY);
+        if (!wait_reserve(S, q, est)) return preempted();
+        pb_config cfg{};
+        cfg.max_tuple_bytes = (int64_t)(S->budget / 2);  // larger products run in row panels
+        pb_status st = pb_spgemm_symbolic(hd, &A, &B, (pb_dtype)dtype, &cfg, ps, &h.plan);
+        unreserve(S, est);
+        if (st != PB_OK) {
+            h.plan = nullptr;
+            return fail(st);
+        }
+        h.plan_bytes = plan_device_bytes(h.plan);
+        force_reserve(S, h.plan_bytes);
+        int64_t flop = 0;
+        size_t ws_bytes = 0;
+        pb_plan_query(h.plan, &flop, nullptr, &ws_bytes, nullptr, nullptr);
+        const size_t m = (size_t)A.nrows;
+        const size_t rp = intermediate ? 4 : 8;
+        auto out_bytes = [&](int64_t cap) {
+            const size_t c = (size_t)std::max<int64_t>(cap, 1);
+            return r256(rp * (m + 1)) + r256(4 * c) + r256(vb * c);
+        };
+        const size_t fixed = h.plan_bytes + held_prev + r256(ws_bytes) + 256;
+        if (fixed > S->budget) return fail(PB_ERR_BUSY);
+        int64_t cap = flop;
+        if (fixed + out_bytes(flop) > S->budget) {
+            // size C exactly first: the counting run needs only the workspace
+            if (!wait_reserve(S, q, r256(ws_bytes) + 256)) return preempted();
+            left = r256(ws_bytes) + 256;
+            if ((st = alloc(S, s, h.ws, r256(ws_bytes), &left)) != PB_OK) return fail(st);
+            if ((st = alloc(S, s, h.nnz, 256, &left)) != PB_OK) return fail(st);
+            pb_csr_out Cc{A.nrows, B.ncols, 0, nullptr, nullptr, nullptr, nullptr, static_cast<int64_t *>(h.nnz.p)};
+            pb_status dev = PB_OK;
+            st = pb_spgemm_numeric(hd, h.plan, &A, &B, &Cc, h.ws.p, h.ws.bytes, ps);
+            if (st == PB_OK) st = pb_plan_status(h.plan, ps, &dev);
+            if (st == PB_OK) st = dev;
+            int64_t nnz = 0;
+            if (st == PB_OK) st = read_nnz(s, h.nnz, &nnz);
+            if (st != PB_OK) return fail(st);
+            cap = nnz;
+        }
+        if (fixed + out_bytes(cap) > S->budget) return fail(PB_ERR_BUSY);
+        // what the step still lacks, reserved together
+        const size_t lack = (h.ws.p ? 0 : r256(ws_bytes)) + (h.nnz.p ? 0 : 256) + out_bytes(cap);
+        if (!wait_reserve(S, q, lack)) return preempted();
+        left = lack;
+        if (!h.ws.p && (st = alloc(S, s, h.ws, r256(ws_bytes), &left)) != PB_OK) return fail(st);
+        if (!h.nnz.p && (st = alloc(S, s, h.nnz, 256, &left)) != PB_OK) return fail(st);
+        const size_t c = (size_t)std::max<int64_t>(cap, 1);
+        if ((st = alloc(S, s, h.out_rowptr, r256(rp * (m + 1)), &left)) != PB_OK) return fail(st);
+        if ((st = alloc(S, s, h.out_colidx, r256(4 * c), &left)) != PB_OK) return fail(st);
+        if ((st = alloc(S, s, h.out_val, r256(vb * c), &left)) != PB_OK) return fail(st);
+        pb_csr_out C{A.nrows, B.ncols, cap, intermediate ? nullptr : static_cast<int64_t *>(h.out_rowptr.p),
+                     intermediate ? static_cast<int32_t *>(h.out_rowptr.p) : nullptr,
+                     static_cast<int32_t *>(h.out_colidx.p), h.out_val.p, static_cast<int64_t *>(h.nnz.p)};
+        pb_status dev = PB_OK;
+        st = pb_spgemm_numeric(hd, h.plan, &A, &B, &C, h.ws.p, h.ws.bytes, ps);
+        if (st == PB_OK) st = pb_plan_status(h.plan, ps, &dev);  // synchronises this slot's stream only
+        if (st == PB_OK) st = dev;
+        int64_t nnz = 0;
+        if (st == PB_OK) st = read_nnz(s, h.nnz, &nnz);
+        if (st != PB_OK) return fail(st);
+        drop_step(S, s, h);
+        if (intermediate) {
+            for (Buf *b : {&h.prev_rowptr, &h.prev_colidx, &h.prev_val}) put(S, s, *b);
+            h.prev_rowptr = h.out_rowptr;
+            h.prev_colidx = h.out_colidx;
+            h.prev_val = h.out_val;
+            h.prev_nnz = nnz;
+            h.out_rowptr = h.out_colidx = h.out_val = Buf{};
+        } else {
+            q->nnz = nnz;
         }
     }
+    for (Buf *b : {&h.prev_rowptr, &h.prev_colidx, &h.prev_val}) put(S, s, *b);
+    q->out_rowptr = h.out_rowptr;
+    q->out_colidx = h.out_colidx;
+    q->out_val = h.out_val;
+    *status = PB_OK;
+    return OK_DONE;
 }
 
-void preempt(pb_server *S, Req *q) {
-    release_all(S, q);
-    std::lock_guard<std::mutex> lk(S->mu);
-    if (q->slot >= 0) S->slots[q->slot] = nullptr;
-    q->slot = -1;
-    q->step = 0;
-    q->phase = QUEUED;
-    q->waiting = false;
-    q->counted = false;
-    q->prev_nnz = 0;
-    ++q->restarts;
-    ++S->preempted;
-    S->queue.push_front(q);
-}
-
-void worker_main(pb_server *S) {
+void slot_main(SlotCtx c) {
+    pb_server *S = c.S;
+    const int slot = c.slot;
     (void)cudaSetDevice(S->device);
     std::unique_lock<std::mutex> lk(S->mu);
     for (;;) {
-        bool progress = false;
-        // results and requests released by callers (no request is referenced here)
-        if (!S->to_free.empty() || !S->to_delete.empty()) {
-            std::vector<Buf> fr;
-            std::vector<Req *> dl;
-            fr.swap(S->to_free);
-            dl.swap(S->to_delete);
-            lk.unlock();
-            for (Buf &b : fr) (void)cudaFreeAsync(b.p, S->streams[0]);
-            for (Req *q : dl) {
-                if (q->ev) (void)cudaEventDestroy(q->ev);
-                delete q;
-            }
-            lk.lock();
-            progress = true;
-        }
-        // admitted requests: completed events and retries after waiting for memory
-        for (int i = 0; i < S->max_slots; ++i) {
-            Req *q = S->slots[i];
-            if (!q) continue;
-            if (q->phase == COUNTING || q->phase == RUNNING) {
-                lk.unlock();
-                const cudaError_t e = cudaEventQuery(q->ev);
-                bool fired = e == cudaSuccess;
-                if (e != cudaSuccess && e != cudaErrorNotReady) {
-                    (void)cudaGetLastError();
-                    finish(S, q, PB_ERR_CUDA);
-                    fired = false;
-                    progress = true;
-                }
-                if (fired) {
-                    advance(S, q);
-                    progress = true;
-                }
-                lk.lock();
-            } else if (q->phase == PLAN || q->phase == MEM) {
-                lk.unlock();
-                const bool moved = advance(S, q);
-                lk.lock();
-                q->waiting = !moved && q->phase != DONE;
-                progress |= moved;
-            }
-        }
-        // preemption: every admitted request waits for memory
-        int active = 0, waiting = 0;
-        Req *youngest = nullptr;
-        for (Req *q : S->slots) {
-            if (!q) continue;
-            ++active;
-            if (q->waiting) {
-                ++waiting;
-                if (!youngest || q->t_admit > youngest->t_admit) youngest = q;
-            }
-        }
-        if (active >= 2 && waiting == active) {
-            lk.unlock();
-            preempt(S, youngest);
-            lk.lock();
-            progress = true;
+        if (S->queue.empty() || S->waiting > 0) {
+            if (S->stop && S->queue.empty()) break;
+            S->cv_work.wait_for(lk, std::chrono::milliseconds(5));
             continue;
         }
-        // admissions, in arrival order, while nobody waits for memory
-        while (waiting == 0 && !S->queue.empty()) {
-            int free_slot = -1;
-            for (int i = 0; i < S->max_slots; ++i)
-                if (!S->slots[i]) {
-                    free_slot = i;
-                    break;
-                }
-            if (free_slot < 0) break;
-            Req *q = S->queue.front();
-            S->queue.pop_front();
-            S->slots[free_slot] = q;
-            q->slot = free_slot;
-            q->phase = PLAN;
-            q->t_admit = Clock::now();
-            if (!q->admitted_once) {
-                q->admitted_once = true;
-                q->t_first_admit = q->t_admit;
-            }
-            lk.unlock();
-            const bool moved = advance(S, q);
-            lk.lock();
-            q->waiting = !moved && q->phase != DONE;
-            if (q->waiting) waiting = 1;
-            progress = true;
+        // least estimated work first, within a bounded bypass of the oldest request
+        size_t pick = 0;
+        if (S->queue.front()->bypassed < MAX_BYPASS) {
+            for (size_t i = 1; i < S->queue.size(); ++i)
+                if (S->queue[i]->est < S->queue[pick]->est) pick = i;
         }
-        bool busy = !S->queue.empty();
-        for (Req *q : S->slots) busy |= q != nullptr;
-        if (S->stop && !busy && S->to_free.empty() && S->to_delete.empty()) break;
-        if (!progress) S->cv_work.wait_for(lk, std::chrono::microseconds(busy ? 20 : 2000));
+        Req *q = S->queue[pick];
+        for (size_t i = 0; i < pick; ++i) ++S->queue[i]->bypassed;
+        S->queue.erase(S->queue.begin() + (std::ptrdiff_t)pick);
+        S->active[slot] = q;
+        q->preempt = false;
+        q->t_admit = Clock::now();
+        if (!q->admitted_once) {
+            q->admitted_once = true;
+            q->t_first_admit = q->t_admit;
+        }
+        lk.unlock();
+        pb_status st = PB_OK;
+        const Outcome o = run(S, slot, q, &st);
+        if (o != PREEMPTED) finish(S, q, st);
+        lk.lock();
+        S->active[slot] = nullptr;
+        if (o == PREEMPTED) {
+            ++q->restarts;
+            ++S->preempted;
+            S->queue.push_front(q);
+        }
+        S->cv_work.notify_all();
     }
 }
 
@@ -497,6 +410,15 @@ pb_status check_request(pb_server *S, const pb_request *r) {
 Req *find(pb_server *S, uint64_t id) {
     auto it = S->reqs.find(id);
     return it == S->reqs.end() ? nullptr : it->second;
+}
+
+void free_result(pb_server *S, Req *q) {
+    for (Buf *b : {&q->out_rowptr, &q->out_colidx, &q->out_val})
+        if (b->p) {
+            (void)cudaFreeAsync(b->p, S->streams[0]);
+            S->in_use -= std::min(b->bytes, S->in_use);
+            *b = Buf{};
+        }
 }
 
 }  // namespace
@@ -524,25 +446,28 @@ pb_status pb_server_create(pb_handle *h, size_t hbm_budget, int32_t max_slots, p
         uint64_t keep = hbm_budget;  // keep freed memory in the pool up to the budget
         e = cudaMemPoolSetAttribute(S->pool, cudaMemPoolAttrReleaseThreshold, &keep);
     }
-    for (int i = 0; e == cudaSuccess && i < max_slots; ++i) {
+    pb_status st = PB_OK;
+    for (int i = 0; e == cudaSuccess && st == PB_OK && i < max_slots; ++i) {
         cudaStream_t s = nullptr;
         e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
-        if (e == cudaSuccess) S->streams.push_back(s);
+        if (e != cudaSuccess) break;
+        S->streams.push_back(s);
+        pb_handle *hs = nullptr;
+        st = pb_create(&hs);
+        if (st == PB_OK) st = pb_set_allocator(hs, pool_alloc, pool_free, S);
+        if (hs) S->hs.push_back(hs);
     }
-    pb_status st = PB_OK;
-    if (e == cudaSuccess) st = pb_create(&S->h);
-    if (e == cudaSuccess && st == PB_OK) st = pb_set_allocator(S->h, pool_alloc, pool_free, S);
     cudaSetDevice(prev);
     if (e != cudaSuccess || st != PB_OK) {
         for (cudaStream_t s : S->streams) cudaStreamDestroy(s);
+        for (pb_handle *x : S->hs) pb_destroy(x);
         if (S->pool) cudaMemPoolDestroy(S->pool);
-        if (S->h) pb_destroy(S->h);
         delete S;
         if (e != cudaSuccess) return host_cuda_fail(h, e, "pb_server_create");
         return st;
     }
-    S->slots.assign(max_slots, nullptr);
-    S->worker = std::thread(worker_main, S);
+    S->active.assign(max_slots, nullptr);
+    for (int i = 0; i < max_slots; ++i) S->threads.emplace_back(slot_main, SlotCtx{S, i});
     *out = S;
     return PB_OK;
 }
@@ -554,22 +479,19 @@ pb_status pb_server_destroy(pb_server *S) {
         S->stop = true;
     }
     S->cv_work.notify_all();
-    S->worker.join();
+    for (std::thread &t : S->threads) t.join();
     int prev = 0;
     cudaGetDevice(&prev);
     cudaSetDevice(S->device);
     for (auto &kv : S->reqs) {
-        Req *q = kv.second;
-        for (Buf *b : {&q->out_rowptr, &q->out_colidx, &q->out_val})
-            if (b->p) cudaFreeAsync(b->p, S->streams[0]);
-        if (q->ev) cudaEventDestroy(q->ev);
-        delete q;
+        free_result(S, kv.second);
+        delete kv.second;
     }
     for (cudaStream_t s : S->streams) {
         cudaStreamSynchronize(s);
         cudaStreamDestroy(s);
     }
-    pb_destroy(S->h);
+    for (pb_handle *x : S->hs) pb_destroy(x);
     cudaMemPoolDestroy(S->pool);
     cudaSetDevice(prev);
     delete S;
@@ -586,15 +508,8 @@ pb_status pb_serve_submit(pb_server *S, const pb_request *r, uint64_t *req_id) {
     if (!q) return PB_ERR_OOM;
     q->r = *r;
     q->nsteps = r->kind == PB_REQ_GALERKIN ? 2 : 1;
-    int prev = 0;
-    cudaGetDevice(&prev);
-    cudaSetDevice(S->device);
-    cudaError_t e = cudaEventCreateWithFlags(&q->ev, cudaEventDisableTiming);
-    cudaSetDevice(prev);
-    if (e != cudaSuccess) {
-        delete q;
-        return host_cuda_fail(S->user, e, "pb_serve_submit");
-    }
+    const double rowB = r->B.nrows > 0 ? (double)r->B.nnz / (double)r->B.nrows : 0.0;
+    q->est = (double)r->A.nnz * std::max(rowB, 1.0) * q->nsteps;
     q->t_submit = Clock::now();
     {
         std::lock_guard<std::mutex> lk(S->mu);
@@ -612,8 +527,8 @@ pb_status pb_serve_poll(pb_server *S, uint64_t id, int32_t *done, pb_status *res
     std::lock_guard<std::mutex> lk(S->mu);
     Req *q = find(S, id);
     if (!q) return PB_ERR_INVALID_ARG;
-    *done = q->phase == DONE ? 1 : 0;
-    if (result) *result = q->phase == DONE ? q->result : PB_OK;
+    *done = q->done ? 1 : 0;
+    if (result) *result = q->done ? q->result : PB_OK;
     return PB_OK;
 }
 
@@ -622,7 +537,7 @@ pb_status pb_serve_wait(pb_server *S, uint64_t id, pb_status *result) {
     std::unique_lock<std::mutex> lk(S->mu);
     Req *q = find(S, id);
     if (!q) return PB_ERR_INVALID_ARG;
-    S->cv_done.wait(lk, [&] { return q->phase == DONE; });
+    S->cv_done.wait(lk, [&] { return q->done; });
     if (result) *result = q->result;
     return PB_OK;
 }
@@ -631,11 +546,10 @@ pb_status pb_serve_result(pb_server *S, uint64_t id, pb_csr_out *C) {
     if (!S || !C) return PB_ERR_INVALID_ARG;
     std::lock_guard<std::mutex> lk(S->mu);
     Req *q = find(S, id);
-    if (!q || q->phase != DONE || q->result != PB_OK) return PB_ERR_INVALID_ARG;
+    if (!q || !q->done || q->result != PB_OK) return PB_ERR_INVALID_ARG;
     const pb_request &r = q->r;
-    const int32_t nrows = r.kind == PB_REQ_GALERKIN ? r.B.ncols : r.A.nrows;
     std::memset(C, 0, sizeof(*C));
-    C->nrows = nrows;
+    C->nrows = r.kind == PB_REQ_GALERKIN ? r.B.ncols : r.A.nrows;
     C->ncols = r.B.ncols;
     C->cap = q->nnz;
     C->rowptr64 = static_cast<int64_t *>(q->out_rowptr.p);
@@ -648,7 +562,7 @@ pb_status pb_serve_timing(pb_server *S, uint64_t id, double *queued_ms, double *
     if (!S) return PB_ERR_INVALID_ARG;
     std::lock_guard<std::mutex> lk(S->mu);
     Req *q = find(S, id);
-    if (!q || q->phase != DONE) return PB_ERR_INVALID_ARG;
+    if (!q || !q->done) return PB_ERR_INVALID_ARG;
     using ms = std::chrono::duration<double, std::milli>;
     if (queued_ms) *queued_ms = q->admitted_once ? ms(q->t_first_admit - q->t_submit).count() : 0.0;
     if (total_ms) *total_ms = ms(q->t_done - q->t_submit).count();
@@ -657,18 +571,21 @@ pb_status pb_serve_timing(pb_server *S, uint64_t id, double *queued_ms, double *
 
 pb_status pb_serve_release(pb_server *S, uint64_t id) {
     if (!S) return PB_ERR_INVALID_ARG;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(S->device);
     {
         std::lock_guard<std::mutex> lk(S->mu);
         Req *q = find(S, id);
-        if (!q || q->phase != DONE) return PB_ERR_INVALID_ARG;
-        for (Buf *b : {&q->out_rowptr, &q->out_colidx, &q->out_val})
-            if (b->p) {
-                S->to_free.push_back(*b);
-                S->in_use -= std::min(b->bytes, S->in_use);
-            }
+        if (!q || !q->done) {
+            cudaSetDevice(prev);
+            return PB_ERR_INVALID_ARG;
+        }
+        free_result(S, q);  // the slot that ran q no longer touches it once it is done
         S->reqs.erase(id);
-        S->to_delete.push_back(q);
+        delete q;
     }
+    cudaSetDevice(prev);
     S->cv_work.notify_all();
     return PB_OK;
 }

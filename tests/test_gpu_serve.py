@@ -168,12 +168,35 @@ def drain(srv, ids, check):
         time.sleep(0.001)
 
 
+def step_needs(pb, r):
+    """Per product step of a request: (bytes with an exact C, bytes with a flop-sized C), as the server counts."""
+    kind, A, B, dt, Ad, Bd = r
+    vb = 8 if dt == pb.PB_F64 else 4
+    steps = [(A, B, Ad, Bd, 4 if kind == "galerkin" else 8)]
+    if kind == "galerkin":
+        AP = oracle.spgemm(A, B)
+        APc = synth.CSR(A.nrows, B.ncols, AP.rowptr.astype(np.int32), AP.colidx, AP.val)
+        steps.append((synth.transpose_csr_as_csc(B), APc, pb.CscMatrix(B.ncols, B.nrows, Bd.rowptr, Bd.colidx, Bd.val),
+                      pb.csr_to_device(APc), 8))
+    out = []
+    held = 0
+    for A1, B1, A1d, B1d, rp in steps:
+        plan = pb.symbolic(A1d, B1d, dtype=dt)
+        nnz = oracle.spgemm(A1, B1).nnz
+        base = held + 16 * (A1.ncols + 2) + 96 * (A1.nrows + 2) + 12 * A1.nnz + (1 << 20) + plan.workspace_bytes
+        base += rp * (A1.nrows + 1) + 4096
+        out.append((base + (4 + vb) * nnz, base + (4 + vb) * plan.flop))
+        held = rp * (A1.nrows + 1) + (4 + vb) * nnz + 1024
+    return out
+
+
 def test_tight_budget_counting_runs_and_preemption(pb):
-    """A budget just above the largest request: outputs sized by counting runs, requests wait or are
-    preempted, and the server never holds more than the budget."""
+    """A budget that holds the largest request only with an exactly sized C: the largest requests are
+    sized by counting runs, the others wait or are preempted, and the budget is never exceeded."""
     reqs = mixed_requests(pb, 2)
-    need = max(20 * oracle.flop(A, B) + 256 * A.nrows + 16 * A.nnz for _, A, B, _, _, _ in reqs)
-    budget = need + (2 << 20)
+    needs = [n for r in reqs for n in step_needs(pb, r)]
+    budget = max(exact for exact, _ in needs) + (1 << 20)
+    assert any(flop_sized > budget for _, flop_sized in needs)   # some steps must count first
     srv = pb.Server(budget, max_slots=4)
     ids = [submit(srv, r) for r in reqs]
 
