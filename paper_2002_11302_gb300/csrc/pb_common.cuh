@@ -166,6 +166,11 @@ __device__ inline void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint
         : "memory");
 }
 
+// Prefetch `bytes` (a multiple of 16) at a 16-byte aligned global address into L2.
+__device__ inline void bulk_prefetch_l2(const void *src, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
+
 // ---------------------------------------------------------------------------
 // Block-wide scans.
 // ---------------------------------------------------------------------------

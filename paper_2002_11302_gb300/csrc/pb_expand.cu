@@ -76,8 +76,15 @@ __device__ inline Batch<IV> load_batch(const NumericArgs &p, const IV *__restric
 // BATCH: the work items of all products of a batch, one product per item;
 // A entries are indexed in the batch's global entry space and the operand
 // arrays of the item's product are taken from its descriptor.
+#ifndef PB_EXPAND_U
+#define PB_EXPAND_U 1  // 32-tuple steps whose B loads are issued together
+#endif
+#ifndef PB_EXPAND_MINB
+#define PB_EXPAND_MINB 5  // resident blocks per SM the register budget must allow (measured best on GB300)
+#endif
+
 template <class IV, class TV, bool BATCH>
-__global__ void __launch_bounds__(256) k_expand(const NumericArgs p) {
+__global__ void __launch_bounds__(256, PB_EXPAND_MINB) k_expand(const NumericArgs p) {
     const int lane = threadIdx.x & 31;
     const int64_t gwarp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -121,27 +128,42 @@ __global__ void __launch_bounds__(256) k_expand(const NumericArgs p) {
             // ---- short runs as one flattened stream --------------------------------
             const int32_t incl = warp_inclusive_scan(sl);
             const int32_t total = __shfl_sync(FULL, incl, 31);
-            for (int32_t t0 = 0; t0 < total; t0 += 32) {
-                const int32_t t = t0 + lane;
-                int r = 0;  // the run holding tuple t: number of runs ending at or before t
+            // Steps of 32 tuples in groups of PB_EXPAND_U: the B loads of a group
+            // are all issued before any of its stores, so their latencies overlap.
+            for (int32_t t0 = 0; t0 < total; t0 += 32 * PB_EXPAND_U) {
+                uint32_t col[PB_EXPAND_U];
+                IV bv[PB_EXPAND_U];
+                int rr[PB_EXPAND_U];
+                int32_t ibs[PB_EXPAND_U];
 #pragma unroll
-                for (int s = 16; s >= 1; s >>= 1)
-                    if (__shfl_sync(FULL, incl, r + s - 1) <= t) r += s;
-                const int32_t ib = t - (__shfl_sync(FULL, incl, r) - __shfl_sync(FULL, sl, r));
-                const int32_t br = __shfl_sync(FULL, cur.b0, r);
-                const uint32_t keyhi = (uint32_t)__shfl_sync(FULL, (uint32_t)cur.info, r);
-                const IV ar = __shfl_sync(FULL, cur.av, r);
-                const bool act = t < total;
-                uint32_t col = 0;
-                IV bv = IV(0);
-                if (act) {
-                    col = (uint32_t)colidxB[br + ib];
-                    bv = valB[br + ib];
+                for (int u = 0; u < PB_EXPAND_U; ++u) {
+                    const int32_t t = t0 + 32 * u + lane;
+                    int r = 0;  // the run holding tuple t: number of runs ending at or before t
+#pragma unroll
+                    for (int s = 16; s >= 1; s >>= 1)
+                        if (__shfl_sync(FULL, incl, r + s - 1) <= t) r += s;
+                    const int32_t ib = t - (__shfl_sync(FULL, incl, r) - __shfl_sync(FULL, sl, r));
+                    const int32_t br = __shfl_sync(FULL, cur.b0, r);
+                    col[u] = 0;
+                    bv[u] = IV(0);
+                    if (t < total) {
+                        col[u] = (uint32_t)colidxB[br + ib];
+                        bv[u] = valB[br + ib];
+                    }
+                    rr[u] = r;
+                    ibs[u] = ib;
                 }
-                const int64_t pr = __shfl_sync(FULL, pos, r);
-                if (act && pr >= 0) {
-                    keys[pr + ib] = keyhi | col;
-                    vals[pr + ib] = tuple_product<TV, IV>(ar, bv);
+#pragma unroll
+                for (int u = 0; u < PB_EXPAND_U; ++u) {
+                    const int32_t t = t0 + 32 * u + lane;
+                    const int r = rr[u];
+                    const uint32_t keyhi = (uint32_t)__shfl_sync(FULL, (uint32_t)cur.info, r);
+                    const IV ar = __shfl_sync(FULL, cur.av, r);
+                    const int64_t pr = __shfl_sync(FULL, pos, r);
+                    if (t < total && pr >= 0) {
+                        keys[pr + ibs[u]] = keyhi | col[u];
+                        vals[pr + ibs[u]] = tuple_product<TV, IV>(ar, bv[u]);
+                    }
                 }
             }
             // ---- long runs, one per warp step -------------------------------------
