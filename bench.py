@@ -701,7 +701,7 @@ def run_ours(args, w):
     handle = binding.Handle()
     stream = torch.cuda.current_stream()
     cfg = binding.make_config(bin_capacity=args.capacity, expand_chunk=args.chunk,
-                              max_tuple_bytes=w.get("budget", 0))
+                              max_tuple_bytes=w.get("budget", 0), deterministic=args.deterministic)
     dt = {"f64": binding.PB_F64, "f64_f32tuple": binding.PB_F64_F32TUPLE}[w["dtype"]]
     plan = binding.symbolic(Ad, Bd, dtype=dt, config=cfg, handle=handle)
     flop = plan.flop
@@ -788,7 +788,7 @@ def run_ours(args, w):
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64" if dt == binding.PB_F64 else "f64 (f32 tuples)", "data": "synthetic",
         "config": {"workload": w["desc"], "n": A.nrows, "nnz_a": A.nnz, "flop": flop, "nnz_c": nnz_c,
-                   "npanels": plan.npanels, "tuple_bytes": tuple_bytes,
+                   "npanels": plan.npanels, "tuple_bytes": tuple_bytes, "deterministic": args.deterministic,
                    "cf": flop / max(nnz_c, 1), "nbins": plan.nbins, "bin_capacity": args.capacity or 4096,
                    "l2": "no flush: the inputs and the tuple buffer each exceed the 129 MB L2",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
@@ -876,6 +876,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="batch workload: skip the autotuner")
+    ap.add_argument("--deterministic", action="store_true",
+                    help="single products: fixed tuple positions, bitwise-reproducible values")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     w = WORKLOADS[args.workload]

@@ -96,7 +96,11 @@ typedef struct pb_config {
     int32_t bin_capacity;    /* max tuples of one bin sorted on-chip (power of two, 1024..16384) */
     int32_t sort_threads;    /* threads of one sort CTA (256 or 512)                           */
     int32_t expand_chunk;    /* tuples per expand work item                                     */
-    int32_t reserved0;
+    int32_t deterministic;   /* nonzero: bitwise-reproducible values.  The plan fixes every A entry's
+                                tuple positions (CSC order inside each bin) instead of atomic cursors,
+                                and equal keys merge in position order, so every C(i,j) is summed over
+                                ascending k, identically on every run (costs a stable sort of A's
+                                entries in the symbolic phase and 8 bytes per entry of A in the plan) */
     int64_t max_tuple_bytes; /* cap on the tuple workspace (tuples plus the global-sort scratch of
                                 oversize rows); a larger product runs in row panels, consecutive
                                 bin ranges processed one after another                            */

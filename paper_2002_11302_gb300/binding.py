@@ -54,7 +54,7 @@ class _CSROut(ctypes.Structure):
 
 class _Config(ctypes.Structure):
     _fields_ = [("bin_capacity", ctypes.c_int32), ("sort_threads", ctypes.c_int32),
-                ("expand_chunk", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+                ("expand_chunk", ctypes.c_int32), ("deterministic", ctypes.c_int32),
                 ("max_tuple_bytes", ctypes.c_int64), ("reserved1", ctypes.c_int64)]
 
 
@@ -262,8 +262,9 @@ def default_handle() -> Handle:
     return _default_handle
 
 
-def make_config(bin_capacity: int = 0, expand_chunk: int = 0, max_tuple_bytes: int = 0) -> _Config:
-    return _Config(bin_capacity, 0, expand_chunk, 0, max_tuple_bytes, 0)
+def make_config(bin_capacity: int = 0, expand_chunk: int = 0, max_tuple_bytes: int = 0,
+                deterministic: bool = False) -> _Config:
+    return _Config(bin_capacity, 0, expand_chunk, 1 if deterministic else 0, max_tuple_bytes, 0)
 
 
 class Plan:

@@ -17,7 +17,7 @@ SRC_DIR = os.path.join(PKG, "csrc")
 INC_DIR = os.path.join(ROOT, "include")
 OBJ_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libpbspgemm.so")
-SOURCES = ["pb_scan.cu", "pb_symbolic.cu", "pb_expand.cu", "pb_oversize.cu", "pb_binsort.cu", "pb_api.cu", "pb_batch.cu", "pb_serve.cu", "pb_noalloc.cu"]
+SOURCES = ["pb_scan.cu", "pb_symbolic.cu", "pb_expand.cu", "pb_oversize.cu", "pb_binsort.cu", "pb_api.cu", "pb_batch.cu", "pb_serve.cu", "pb_determ.cu", "pb_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INC_DIR]
 

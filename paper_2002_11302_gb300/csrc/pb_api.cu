@@ -41,6 +41,8 @@ struct pb_plan {
     size_t arena_bytes = 0;
     void *chunk_mem = nullptr;
     size_t chunk_bytes = 0;
+    void *apos_mem = nullptr;  // deterministic mode: run position of every A entry
+    size_t apos_bytes = 0;
     int64_t *F = nullptr, *R = nullptr, *flags = nullptr, *bin_off = nullptr, *scan_tmp = nullptr;
     uint64_t *rowinfo = nullptr, *ainfo = nullptr;
     int32_t *bin_row = nullptr, *chunk_e = nullptr, *acol = nullptr;
@@ -117,6 +119,8 @@ pb_status check_operands(pb_handle *h, const pb_csc *A, const pb_csr *B) {
 void free_plan_memory(pb_plan *p) {
     if (!p || !p->h) return;
     if (p->chunk_mem) p->h->free_fn(p->chunk_mem, p->chunk_bytes, nullptr, p->h->ctx);
+    if (p->apos_mem) p->h->free_fn(p->apos_mem, p->apos_bytes, nullptr, p->h->ctx);
+    p->apos_mem = nullptr;
     if (p->over_map_mem) p->h->free_fn(p->over_map_mem, p->over_map_bytes, nullptr, p->h->ctx);
     p->over_map_mem = nullptr;
     if (p->arena) p->h->free_fn(p->arena, p->arena_bytes, nullptr, p->h->ctx);
@@ -129,7 +133,9 @@ namespace pb {
 pb_status host_fail(pb_handle *h, pb_status st, const std::string &msg) { return fail(h, st, msg); }
 pb_status host_cuda_fail(pb_handle *h, cudaError_t e, const char *where) { return cuda_fail(h, e, where); }
 pb_status host_check_operands(pb_handle *h, const pb_csc *A, const pb_csr *B) { return check_operands(h, A, B); }
-size_t plan_device_bytes(const pb_plan *p) { return p ? p->arena_bytes + p->chunk_bytes + p->over_map_bytes : 0; }
+size_t plan_device_bytes(const pb_plan *p) {
+    return p ? p->arena_bytes + p->chunk_bytes + p->over_map_bytes + p->apos_bytes : 0;
+}
 }  // namespace pb
 
 extern "C" {
@@ -337,6 +343,25 @@ pb_status pb_spgemm_symbolic(pb_handle *h, const pb_csc *A, const pb_csr *B, pb_
         cuda_fail(h, e, "chunk table");
         return bail(PB_ERR_CUDA);
     }
+    // Deterministic mode: fixed run positions (CSC order inside each bin).
+    if (cfg && cfg->deterministic && p->nnzA > 0) {
+        p->apos_bytes = align256(8 * (size_t)p->nnzA);
+        p->apos_mem = h->alloc(p->apos_bytes, stream_, h->ctx);
+        const size_t sb = (size_t)det_scratch_bytes(p->nnzA);
+        void *scratch = p->apos_mem ? h->alloc(sb, stream_, h->ctx) : nullptr;
+        if (!scratch) {
+            fail(h, PB_ERR_OOM, "deterministic-mode allocation failed");
+            return bail(PB_ERR_OOM);
+        }
+        DetArgs d{p->nnzA, p->hdr.nbins, p->ainfo, p->acol, B->rowptr, p->bin_row, p->bin_off, p->R,
+                  static_cast<int64_t *>(p->apos_mem)};
+        e = launch_det_positions(d, scratch, h->num_sms, s);
+        h->free_fn(scratch, sb, stream_, h->ctx);
+        if (e != cudaSuccess) {
+            cuda_fail(h, e, "deterministic positions");
+            return bail(PB_ERR_CUDA);
+        }
+    }
     // Row panels: with a tuple budget smaller than the whole product, bins are
     // grouped into consecutive panels whose tuples fit the budget together.
     const size_t per_tuple = 4 + tuple_val_bytes(dtype);
@@ -472,6 +497,7 @@ static pb_status fill_numeric(pb_handle *h, const pb_plan *p, const pb_csc *A, c
     a.bin_off = p->bin_off;
     a.chunk_e = p->chunk_e;
     a.acol = p->acol;
+    a.apos = static_cast<const int64_t *>(p->apos_mem);
     a.flop = p->hdr.flop;
     a.nbins = p->hdr.nbins;
     a.nchunks = p->nchunks;

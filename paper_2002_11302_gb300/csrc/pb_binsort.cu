@@ -354,6 +354,7 @@ __global__ void __launch_bounds__(THREADS, (THREADS <= 256 ? 4 : (THREADS <= 512
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const TV *__restrict__ gvals = static_cast<const TV *>(p.vals);
     OV *__restrict__ valC = static_cast<OV *>(p.valC);
+    const bool stable_ties = p.apos != nullptr;
     int colbits = p.colbits;
     uint32_t colmask = (p.colbits >= 32) ? 0xffffffffu : ((1u << p.colbits) - 1u);
 
@@ -473,22 +474,32 @@ __global__ void __launch_bounds__(THREADS, (THREADS <= 256 ? 4 : (THREADS <= 512
                 }
                 __syncthreads();
                 // Each tuple's final slot: its bucket's start plus the number of
-                // tuples of the same bucket with a smaller key (ties by position).
+                // tuples of the same bucket with a smaller key, ties broken by the
+                // order in the bin in deterministic mode (fixed positions: equal
+                // keys then merge in that order) and by bucket slot otherwise.
                 // Buckets hold a few tuples, so this is a short loop per tuple.
 #pragma unroll
                 for (int j = 0; j < E; ++j) {
                     const int q = tid + j * THREADS;
                     if (q < N) {
                         const uint32_t key = sm.skey[q];
+                        const uint16_t iq = sm.sidx[q];
                         const uint32_t bk = key >> shift;
                         const int lo = (int)sm.cnt[bk], hi = (int)sm.cnt[bk + 1];
                         int rank = lo;
-                        for (int r = lo; r < hi; ++r) {
-                            const uint32_t o = sm.skey[r];
-                            rank += (o < key) || (o == key && r < q);
+                        if (stable_ties) {  // equal keys keep their order in the bin
+                            for (int r = lo; r < hi; ++r) {
+                                const uint32_t o = sm.skey[r];
+                                rank += (o < key) || (o == key && sm.sidx[r] < iq);
+                            }
+                        } else {
+                            for (int r = lo; r < hi; ++r) {
+                                const uint32_t o = sm.skey[r];
+                                rank += (o < key) || (o == key && r < q);
+                            }
                         }
                         sm.kin[rank] = key;
-                        sm.sidx2[rank] = sm.sidx[q];
+                        sm.sidx2[rank] = iq;
                     }
                 }
                 __syncthreads();

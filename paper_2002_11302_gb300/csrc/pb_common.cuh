@@ -314,6 +314,8 @@ struct NumericArgs {
     uint32_t *skeys;
     void *svals;
     int over_passes;
+    // deterministic mode: the first tuple position of each A entry's run (null: atomic cursors)
+    const int64_t *apos;
     // batched products (null for a single product)
     const BatchDesc *desc;
     const int32_t *chunk_prod;  // [nchunks] product of each expand work item
@@ -324,6 +326,17 @@ struct NumericArgs {
 };
 
 cudaError_t launch_expand(const NumericArgs &a, cudaStream_t s);
+
+// Deterministic mode (pb_determ.cu): run positions fixed in CSC order inside each bin.
+struct DetArgs {
+    int64_t E, nbins;
+    const uint64_t *ainfo;
+    const int32_t *acol, *rowptrB, *bin_row;
+    const int64_t *bin_off, *R;
+    int64_t *apos;  // [E] output
+};
+int64_t det_scratch_bytes(int64_t E);
+cudaError_t launch_det_positions(const DetArgs &d, void *scratch, int num_sms, cudaStream_t s);
 
 cudaError_t launch_binsort(const NumericArgs &a, cudaStream_t s);
 // Batched forms: work counts are read from a.bhdr on the device; the grids are

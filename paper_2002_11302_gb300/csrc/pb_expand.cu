@@ -50,9 +50,10 @@ struct Batch {  // one A entry per lane
     uint64_t info;
     IV av;
     int32_t b0, lb;
+    int64_t apos;  // deterministic mode: the run's fixed first position
 };
 
-template <class IV>
+template <class IV, bool DET>
 __device__ inline Batch<IV> load_batch(const NumericArgs &p, const IV *__restrict__ valA,
                                       const int32_t *__restrict__ rowptrB, int32_t e, bool valid) {
     Batch<IV> x;
@@ -60,6 +61,7 @@ __device__ inline Batch<IV> load_batch(const NumericArgs &p, const IV *__restric
     x.av = IV(0);
     x.b0 = 0;
     x.lb = 0;
+    x.apos = 0;
     if (valid) {
         const int32_t k = p.acol[e];
         x.info = p.ainfo[e];
@@ -68,14 +70,12 @@ __device__ inline Batch<IV> load_batch(const NumericArgs &p, const IV *__restric
             x.av = valA[e];
             x.b0 = rowptrB[k];
             x.lb = rowptrB[k + 1] - x.b0;
+            if (DET) x.apos = p.apos[e];
         }
     }
     return x;
 }
 
-// BATCH: the work items of all products of a batch, one product per item;
-// A entries are indexed in the batch's global entry space and the operand
-// arrays of the item's product are taken from its descriptor.
 #ifndef PB_EXPAND_U
 #define PB_EXPAND_U 1  // 32-tuple steps whose B loads are issued together
 #endif
@@ -83,7 +83,12 @@ __device__ inline Batch<IV> load_batch(const NumericArgs &p, const IV *__restric
 #define PB_EXPAND_MINB 5  // resident blocks per SM the register budget must allow (measured best on GB300)
 #endif
 
-template <class IV, class TV, bool BATCH>
+// BATCH: the work items of all products of a batch, one product per item;
+// A entries are indexed in the batch's global entry space and the operand
+// arrays of the item's product are taken from its descriptor.
+// DET: runs go to positions fixed in the plan (deterministic mode) instead of
+// being reserved at the bins' cursors.
+template <class IV, class TV, bool BATCH, bool DET>
 __global__ void __launch_bounds__(256, PB_EXPAND_MINB) k_expand(const NumericArgs p) {
     const int lane = threadIdx.x & 31;
     const int64_t gwarp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -115,16 +120,16 @@ __global__ void __launch_bounds__(256, PB_EXPAND_MINB) k_expand(const NumericArg
             e_begin = min(e_begin, e_last);
             e_end = min(e_end, e_last);
         }
-        Batch<IV> cur = load_batch(p, valA, rowptrB, e_begin + lane, e_begin + lane < e_end);
+        Batch<IV> cur = load_batch<IV, DET>(p, valA, rowptrB, e_begin + lane, e_begin + lane < e_end);
         for (int32_t e0 = e_begin; e0 < e_end; e0 += 32) {
             const bool valid = e0 + lane < e_end;
             const bool is_long = cur.lb >= LONG_RUN;
             const int32_t sl = is_long ? 0 : cur.lb;
             int64_t pos = -1;
-            if (sl > 0) pos = reserve(p, (uint32_t)(cur.info >> 32), (uint32_t)sl);
+            if (sl > 0) pos = DET ? cur.apos : reserve(p, (uint32_t)(cur.info >> 32), (uint32_t)sl);
             // software pipeline: the next batch's loads overlap this batch's reservations and writes
             const int32_t en = e0 + 32 + lane;
-            const Batch<IV> nxt = load_batch(p, valA, rowptrB, en, en < e_end);
+            const Batch<IV> nxt = load_batch<IV, DET>(p, valA, rowptrB, en, en < e_end);
             // ---- short runs as one flattened stream --------------------------------
             const int32_t incl = warp_inclusive_scan(sl);
             const int32_t total = __shfl_sync(FULL, incl, 31);
@@ -176,8 +181,12 @@ __global__ void __launch_bounds__(256, PB_EXPAND_MINB) k_expand(const NumericArg
                 const int32_t br = __shfl_sync(FULL, cur.b0, r);
                 const int32_t lr = __shfl_sync(FULL, cur.lb, r);
                 int64_t pr = 0;
-                if (lane == 0) pr = reserve(p, (uint32_t)(ir >> 32), (uint32_t)lr);
-                pr = __shfl_sync(FULL, pr, 0);
+                if (DET) {
+                    pr = __shfl_sync(FULL, cur.apos, r);
+                } else {
+                    if (lane == 0) pr = reserve(p, (uint32_t)(ir >> 32), (uint32_t)lr);
+                    pr = __shfl_sync(FULL, pr, 0);
+                }
                 if (pr < 0) continue;
                 const uint32_t keyhi = (uint32_t)ir;
                 for (int32_t ib = lane; ib < lr; ib += 32) {
@@ -199,11 +208,21 @@ cudaError_t launch_expand(const NumericArgs &a, cudaStream_t s) {
     const int64_t need = ceil_div<int64_t>(a.nchunks * 32, threads);
     if (blocks > need) blocks = need;
     if (blocks < 1) blocks = 1;
-    switch (a.dtype) {
-        case PB_F64: k_expand<double, double, false><<<(unsigned)blocks, threads, 0, s>>>(a); break;
-        case PB_F32: k_expand<float, float, false><<<(unsigned)blocks, threads, 0, s>>>(a); break;
-        case PB_F64_F32TUPLE: k_expand<double, float, false><<<(unsigned)blocks, threads, 0, s>>>(a); break;
-        default: return cudaErrorInvalidValue;
+    const unsigned b = (unsigned)blocks;
+    if (a.apos) {
+        switch (a.dtype) {
+            case PB_F64: k_expand<double, double, false, true><<<b, threads, 0, s>>>(a); break;
+            case PB_F32: k_expand<float, float, false, true><<<b, threads, 0, s>>>(a); break;
+            case PB_F64_F32TUPLE: k_expand<double, float, false, true><<<b, threads, 0, s>>>(a); break;
+            default: return cudaErrorInvalidValue;
+        }
+    } else {
+        switch (a.dtype) {
+            case PB_F64: k_expand<double, double, false, false><<<b, threads, 0, s>>>(a); break;
+            case PB_F32: k_expand<float, float, false, false><<<b, threads, 0, s>>>(a); break;
+            case PB_F64_F32TUPLE: k_expand<double, float, false, false><<<b, threads, 0, s>>>(a); break;
+            default: return cudaErrorInvalidValue;
+        }
     }
     count_launches(1);
     return cudaGetLastError();
@@ -217,9 +236,9 @@ cudaError_t launch_expand_batch(const NumericArgs &a, cudaStream_t s) {
     if (blocks > need) blocks = need;
     if (blocks < 1) blocks = 1;
     switch (a.dtype) {
-        case PB_F64: k_expand<double, double, true><<<(unsigned)blocks, threads, 0, s>>>(a); break;
-        case PB_F32: k_expand<float, float, true><<<(unsigned)blocks, threads, 0, s>>>(a); break;
-        case PB_F64_F32TUPLE: k_expand<double, float, true><<<(unsigned)blocks, threads, 0, s>>>(a); break;
+        case PB_F64: k_expand<double, double, true, false><<<(unsigned)blocks, threads, 0, s>>>(a); break;
+        case PB_F32: k_expand<float, float, true, false><<<(unsigned)blocks, threads, 0, s>>>(a); break;
+        case PB_F64_F32TUPLE: k_expand<double, float, true, false><<<(unsigned)blocks, threads, 0, s>>>(a); break;
         default: return cudaErrorInvalidValue;
     }
     count_launches(1);

@@ -131,10 +131,13 @@ bool wait_reserve(pb_server *S, Req *q, size_t b) {
     return true;
 }
 
-void force_reserve(pb_server *S, size_t b) {
+// Replace a reservation of `was` bytes by one of `now` bytes in one step, so no
+// other slot can take the difference in between.
+void swap_reserve(pb_server *S, size_t was, size_t now) {
     std::lock_guard<std::mutex> lk(S->mu);
-    S->in_use += b;
+    S->in_use = S->in_use - std::min(was, S->in_use) + now;
     S->peak = std::max(S->peak, S->in_use);
+    if (now < was) S->cv_work.notify_all();
 }
 
 void unreserve(pb_server *S, size_t b) {
@@ -275,13 +278,13 @@ Outcome run(pb_server *S, int slot, Req *q, pb_status *status) {
         pb_config cfg{};
         cfg.max_tuple_bytes = (int64_t)(S->budget / 2);  // larger products run in row panels
         pb_status st = pb_spgemm_symbolic(hd, &A, &B, (pb_dtype)dtype, &cfg, ps, &h.plan);
-        unreserve(S, est);
         if (st != PB_OK) {
+            unreserve(S, est);
             h.plan = nullptr;
             return fail(st);
         }
         h.plan_bytes = plan_device_bytes(h.plan);
-        force_reserve(S, h.plan_bytes);
+        swap_reserve(S, est, h.plan_bytes);  // the estimate bounds the plan's actual size
         int64_t flop = 0;
         size_t ws_bytes = 0;
         pb_plan_query(h.plan, &flop, nullptr, &ws_bytes, nullptr, nullptr);
