@@ -71,6 +71,21 @@ def make_inputs(w):
     return synth.er(w["n"], w["d"], seed=w["seed"])
 
 
+def combine_replicas(local_ms: float, local_flop: int, device):
+    """Whole-job figures of independent replicas (one per rank): the slowest
+    rank's time and GFLOPS = 2 x all ranks' multiplications / that time.
+    Without an initialised process group this is the single-rank figure."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([local_ms], dtype=torch.float64, device=device)
+    f = torch.tensor([float(local_flop)], dtype=torch.float64, device=device)
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(f, op=dist.ReduceOp.SUM)
+    total_ms = float(t.item())
+    return total_ms, 2.0 * float(f.item()) / (total_ms / 1e3) / 1e9
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -327,12 +342,8 @@ def run_ours_batch(args, w):
     total_ms = t_start.elapsed_time(t_end)
     if bt.status() != 0:
         raise RuntimeError(f"device status {bt.status()} in the timed region")
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms, value = combine_replicas(total_ms, flop * args.steps, "cuda")
     ms_per_step = total_ms / args.steps
-    value = 2.0 * flop * args.steps * world / (total_ms / 1e3) / 1e9
 
     # per-phase kernel times (plain launches with phase events, after the timed region)
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
@@ -761,12 +772,8 @@ def run_ours(args, w):
     total_ms = t_start.elapsed_time(t_end)
     for i in range(args.steps):
         phase_ms["symbolic"] += per_step[i][0].elapsed_time(per_step[i][1])
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms, value = combine_replicas(total_ms, flop * args.steps, "cuda")
     ms_per_step = total_ms / args.steps
-    value = 2.0 * flop * args.steps * world / (total_ms / 1e3) / 1e9
 
     # roofline of the dominant kernel (algorithmic bytes per launch / event-timed duration)
     tuple_bytes = 12 if dt == binding.PB_F64 else 8
