@@ -94,21 +94,24 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def stored_traffic(kernel: str):
-    """DRAM bytes per launch from the committed ncu summary, if still current."""
+def stored_traffic(kernel: str, w, flop: int):
+    """DRAM bytes per launch of `kernel` on an ER FP64 workload: the per-tuple
+    traffic of the committed ncu capture (profiles/traffic.json) times this
+    workload's multiplications, while the kernel source is unchanged; else None."""
+    if w.get("kind") != "er" or w.get("dtype") != "f64":
+        return None
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
     try:
-        j = json.load(open(p))
-        ent = j.get(kernel)
+        import hashlib
+        ent = json.load(open(p)).get(kernel)
         if not ent:
             return None
-        import hashlib
         src = open(os.path.join(ROOT, "paper_2002_11302_gb300", "csrc", ent["source"]), "rb").read()
         if hashlib.sha256(src).hexdigest()[:16] != ent["source_sha"]:
             return None  # kernel changed since the counters were taken
-        return float(ent["dram_bytes_per_launch_scaled"])
+        return float(ent["dram_bytes_per_tuple"]) * flop
     except Exception:  # noqa: BLE001
         return None
 
@@ -801,7 +804,7 @@ def run_ours(args, w):
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "peak_kind": peak_kind,
-                     "traffic": stored_traffic(kname),
+                     "traffic": None if args.deterministic else stored_traffic(kname, w, flop),
                      "alg_bytes_per_launch": bytes_dom, "ms_per_launch": ms_dom},
         "pct_beta_ai": {"numeric": pct_numeric, "step": pct_step, "beta_gbs": hbm, "beta_kind": peak_kind,
                         "ai_flop_per_byte": flop / by.total, "numeric_bytes": by.numeric, "step_bytes": by.total},
