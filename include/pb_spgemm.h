@@ -362,7 +362,7 @@ pb_status pb_serve_stats(pb_server *s, int64_t *completed, int64_t *preempted, s
  * pb_spgemm_numeric (C->cap >= nnz(C); a capacity equal to the product's
  * flop count, sum over k of nnz(A(:,k)) * nnz(B(k,:)), always suffices).
  *
- *   Limit: the plan arrays take about 84*A.nrows + 8*A.ncols + 12*nnz(A)
+ *   Limit: the plan arrays take about 92*A.nrows + 12*A.ncols + 12*nnz(A)
  *   bytes and the tuples 12 (FP64) or 8 (FP32 forms) bytes each, all within
  *   PB_NOALLOC_SCRATCH_BYTES; a larger product returns PB_ERR_WORKSPACE and
  *   launches nothing further.
