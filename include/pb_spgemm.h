@@ -185,6 +185,16 @@ size_t pb_debug_values_offset(const pb_plan *plan);
 
 pb_status pb_plan_destroy(pb_plan *plan);
 
+/* Operand validation: O(nnz(A) + nnz(B)) device checks of the preconditions the
+ * compute calls trust -- colptr / rowptr start at 0, never decrease and end at nnz,
+ * every row index of A lies in [0, A.nrows) and every column index of B in
+ * [0, B.ncols).  Reads each array only within its declared size.  Synchronises
+ * `stream`; *result receives PB_OK or PB_ERR_INVALID_ARG (pb_last_error says which
+ * array is wrong).  Errors (returned): INVALID_ARG, SHAPE, CUDA.  Duplicate entries
+ * inside one column or row are not checked. */
+pb_status pb_validate_operands(pb_handle *h, const pb_csc *A, const pb_csr *B, pb_stream_t stream,
+                               pb_status *result);
+
 /* Measurement hooks (no counterpart in the paper; they only observe).
  * pb_set_phase_events: when events is non-NULL, every later numeric call on
  * this handle records events[0] before its first launch, events[1] after the

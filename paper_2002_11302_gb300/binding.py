@@ -91,6 +91,8 @@ SIGNATURES = {
     "pb_plan_destroy": (ctypes.c_int, [_VP]),
     "pb_set_phase_events": (ctypes.c_int, [_VP, _VP]),
     "pb_kernel_launches": (_I64, []),
+    "pb_validate_operands": (ctypes.c_int, [_VP, ctypes.POINTER(_CSC), ctypes.POINTER(_CSR), _VP,
+                                            ctypes.POINTER(ctypes.c_int)]),
     "pb_spgemm_noalloc": (ctypes.c_int, [ctypes.POINTER(_CSC), ctypes.POINTER(_CSR), ctypes.c_int,
                                          ctypes.POINTER(_CSROut), _VP, ctypes.POINTER(ctypes.c_int)]),
     "pb_spgemm_batch_query": (ctypes.c_int, [_VP, _I32, ctypes.POINTER(_CSC), ctypes.POINTER(_CSR), ctypes.c_int,
@@ -609,3 +611,13 @@ class Server:
 
     def __del__(self):
         self.close()
+
+
+def validate(A: CscMatrix, B: CsrMatrix, handle: Optional[Handle] = None, stream=None):
+    """Device check of the operands' preconditions: (status, message); status 0 = valid."""
+    h = handle or default_handle()
+    cA, cB = A._c(), B._c()
+    res = ctypes.c_int()
+    _check(h.lib, h.ptr, h.lib.pb_validate_operands(h.ptr, ctypes.byref(cA), ctypes.byref(cB), _stream_ptr(stream),
+                                                    ctypes.byref(res)))
+    return int(res.value), (h.lib.pb_last_error(h.ptr).decode() if res.value else "")

@@ -604,6 +604,34 @@ pb_status pb_spgemm_numeric(pb_handle *h, const pb_plan *p, const pb_csc *A, con
     return PB_OK;
 }
 
+pb_status pb_validate_operands(pb_handle *h, const pb_csc *A, const pb_csr *B, pb_stream_t stream_,
+                               pb_status *result) {
+    if (!h || !result) return PB_ERR_INVALID_ARG;
+    h->last_error.clear();
+    pb_status st = check_operands(h, A, B);
+    if (st != PB_OK) return st;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream_);
+    uint32_t *bad = static_cast<uint32_t *>(h->alloc(256, stream_, h->ctx));
+    if (!bad) return fail(h, PB_ERR_OOM, "validation flag");
+    uint32_t word = 0;
+    cudaError_t e = cudaMemsetAsync(bad, 0, 4, s);
+    if (e == cudaSuccess) e = launch_validate(*A, *B, bad, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&word, bad, 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    h->free_fn(bad, 256, stream_, h->ctx);
+    if (e != cudaSuccess) return cuda_fail(h, e, "pb_validate_operands");
+    *result = word ? PB_ERR_INVALID_ARG : PB_OK;
+    if (word) {
+        std::string msg;
+        if (word & 1u) msg += "A.colptr is not a pointer array (0 first, monotone, nnz last); ";
+        if (word & 2u) msg += "B.rowptr is not a pointer array (0 first, monotone, nnz last); ";
+        if (word & 4u) msg += "A.rowidx has an index outside [0, A.nrows); ";
+        if (word & 8u) msg += "B.colidx has an index outside [0, B.ncols); ";
+        h->last_error = msg;
+    }
+    return PB_OK;
+}
+
 pb_status pb_set_phase_events(pb_handle *h, void *const *events) {
     if (!h) return PB_ERR_INVALID_ARG;
     h->phase_on = events != nullptr;

@@ -220,6 +220,10 @@ __device__ inline T block_reduce_sum(T v, T *scratch) {
 int64_t scan_tmp_elems(int64_t n);
 cudaError_t scan_i64(int64_t *x, int64_t n, int64_t *tmp, cudaStream_t s);
 
+// Operand checks of pb_validate_operands; sets bits 1/2 (A.colptr / B.rowptr not
+// a valid pointer array), 4 (A.rowidx out of range), 8 (B.colidx out of range).
+cudaError_t launch_validate(const pb_csc &A, const pb_csr &B, uint32_t *bad, cudaStream_t s);
+
 // Process-wide count of kernels launched by the library (pb_kernel_launches).
 void count_launches(int64_t n);
 

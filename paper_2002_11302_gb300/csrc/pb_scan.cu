@@ -91,3 +91,53 @@ cudaError_t scan_i64(int64_t *x, int64_t n, int64_t *tmp, cudaStream_t s) {
 }
 
 }  // namespace pb
+
+// ---------------------------------------------------------------------------
+// Operand validation (pb_validate_operands): reads each array only within the
+// sizes the caller declared and records what is wrong in a bit mask.
+// ---------------------------------------------------------------------------
+namespace pb {
+namespace {
+
+__global__ void k_validate_ptr(const int32_t *ptr, int64_t n, int64_t nnz, uint32_t bit, uint32_t *bad) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i <= n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t v = ptr[i];
+        bool ok = v >= 0 && v <= nnz;
+        if (i == 0) ok = ok && v == 0;
+        if (i == n) ok = ok && v == nnz;
+        if (i > 0) ok = ok && ptr[i - 1] <= v;
+        if (!ok) atomicOr(bad, bit);
+    }
+}
+
+__global__ void k_validate_idx(const int32_t *idx, int64_t nnz, int32_t bound, uint32_t bit, uint32_t *bad) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nnz; e += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t v = idx[e];
+        if (v < 0 || v >= bound) atomicOr(bad, bit);
+    }
+}
+
+unsigned vgrid(int64_t n) {
+    int64_t g = (n + 255) / 256;
+    if (g > 4096) g = 4096;
+    return (unsigned)(g < 1 ? 1 : g);
+}
+
+}  // namespace
+
+cudaError_t launch_validate(const pb_csc &A, const pb_csr &B, uint32_t *bad, cudaStream_t s) {
+    k_validate_ptr<<<vgrid(A.ncols + 1), 256, 0, s>>>(A.colptr, A.ncols, A.nnz, 1u, bad);
+    k_validate_ptr<<<vgrid(B.nrows + 1), 256, 0, s>>>(B.rowptr, B.nrows, B.nnz, 2u, bad);
+    count_launches(2);
+    if (A.nnz > 0) {
+        k_validate_idx<<<vgrid(A.nnz), 256, 0, s>>>(A.rowidx, A.nnz, A.nrows, 4u, bad);
+        count_launches(1);
+    }
+    if (B.nnz > 0) {
+        k_validate_idx<<<vgrid(B.nnz), 256, 0, s>>>(B.colidx, B.nnz, B.ncols, 8u, bad);
+        count_launches(1);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace pb

@@ -19,44 +19,47 @@ namespace pb {
 
 namespace {
 
-// One thread per column k: f_k = nnz(A(:,k)) * nnz(B(k,:)) (Alg. 3), and the
-// column index of each of its A entries; columns with more than LONG_COL
+// One thread per column k: f_k = nnz(A(:,k)) * nnz(B(k,:)) (Alg. 3), the
+// column index of each of its A entries, and the per-row flop (Sec. III-B):
+// every A(i,k) adds nnz(B(k,:)) to row i.  Columns with more than LONG_COL
 // entries are listed for a warp-wide pass instead.
 constexpr int LONG_COL = 32;
 
-__global__ void k_flop_per_k(int32_t k, const int32_t *colptrA, const int32_t *rowptrB, int64_t *F, int32_t *acol,
-                             int32_t *long_cols, uint32_t *n_long) {
+__device__ inline void add_row_flop(int64_t *R, int32_t row, int64_t lb) {
+    atomicAdd(reinterpret_cast<unsigned long long *>(&R[row]), (unsigned long long)lb);
+}
+
+__global__ void k_flop_per_k(int32_t k, const int32_t *colptrA, const int32_t *rowidxA, const int32_t *rowptrB,
+                             int64_t *F, int64_t *R, int32_t *acol, int32_t *long_cols, uint32_t *n_long) {
     for (int64_t col = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; col < k; col += (int64_t)gridDim.x * blockDim.x) {
         const int32_t a0 = colptrA[col], a1 = colptrA[col + 1];
-        F[col] = (int64_t)(a1 - a0) * ((int64_t)rowptrB[col + 1] - rowptrB[col]);
+        const int64_t lb = (int64_t)rowptrB[col + 1] - rowptrB[col];
+        F[col] = (int64_t)(a1 - a0) * lb;
         if (a1 - a0 > LONG_COL) {
             long_cols[atomicAdd(n_long, 1u)] = (int32_t)col;
         } else {
-            for (int32_t e = a0; e < a1; ++e) acol[e] = (int32_t)col;
+            for (int32_t e = a0; e < a1; ++e) {
+                acol[e] = (int32_t)col;
+                if (lb) add_row_flop(R, rowidxA[e], lb);
+            }
         }
     }
 }
 
-// One warp per listed long column: the column index of each of its entries.
-__global__ void k_acol_long(const int32_t *colptrA, const int32_t *long_cols, const uint32_t *n_long, int32_t *acol) {
+// One warp per listed long column: the same for each of its entries.
+__global__ void k_acol_long(const int32_t *colptrA, const int32_t *rowidxA, const int32_t *rowptrB,
+                            const int32_t *long_cols, const uint32_t *n_long, int64_t *R, int32_t *acol) {
     const int lane = threadIdx.x & 31;
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int64_t n = *n_long;
     for (int64_t i = warp; i < n; i += nwarps) {
         const int32_t col = long_cols[i];
-        for (int32_t e = colptrA[col] + lane; e < colptrA[col + 1]; e += 32) acol[e] = col;
-    }
-}
-
-// Every A(i,k) adds nnz(B(k,:)) to row i (the per-row form of Alg. 3); one
-// thread per A entry.
-__global__ void k_row_flop(int64_t nnzA, const int32_t *acol, const int32_t *rowidxA, const int32_t *rowptrB,
-                           int64_t *R) {
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nnzA; e += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t col = acol[e];
         const int64_t lb = (int64_t)rowptrB[col + 1] - rowptrB[col];
-        if (lb) atomicAdd(reinterpret_cast<unsigned long long *>(&R[rowidxA[e]]), (unsigned long long)lb);
+        for (int32_t e = colptrA[col] + lane; e < colptrA[col + 1]; e += 32) {
+            acol[e] = col;
+            if (lb) add_row_flop(R, rowidxA[e], lb);
+        }
     }
 }
 
@@ -187,16 +190,43 @@ __global__ void k_over_chunk_map(const int64_t *over_chunk_off, int64_t n_over, 
 //   entries tile [0, flop) in CSC order: entry j of column k owns
 //   [F[k] + j*lb, F[k] + (j+1)*lb) with lb = nnz(B(k,:)).  Work item c holds the
 //   entries whose run starts in [c*chunk, (c+1)*chunk): chunk_e[c] is the first.
-__global__ void k_entry_pass(int64_t nnzA, const int32_t *acol, const int32_t *rowidxA, const uint64_t *rowinfo,
-                             const int64_t *F, const int32_t *colptrA, const int32_t *rowptrB, int64_t chunk,
-                             uint64_t *ainfo, int32_t *chunk_e) {
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nnzA; e += (int64_t)gridDim.x * blockDim.x) {
-        ainfo[e] = rowinfo[rowidxA[e]];
-        const int32_t col = acol[e];
+__device__ inline void entry_info(int64_t e, int64_t s, int64_t lb, int64_t chunk, const int32_t *rowidxA,
+                                  const uint64_t *rowinfo, uint64_t *ainfo, int32_t *chunk_e) {
+    ainfo[e] = rowinfo[rowidxA[e]];
+    if (lb == 0) return;
+    const int64_t r = s + lb;
+    for (int64_t c = ceil_div<int64_t>(s, chunk); c * chunk < r; ++c)
+        chunk_e[c] = (c * chunk == s) ? (int32_t)e : (int32_t)(e + 1);
+}
+
+// One thread per short column (the columns of the flop pass): its entries'
+// runs start at F[k], F[k] + lb, ...
+__global__ void k_entry_pass(int32_t k, const int32_t *colptrA, const int32_t *rowidxA, const int32_t *rowptrB,
+                             const uint64_t *rowinfo, const int64_t *F, int64_t chunk, uint64_t *ainfo,
+                             int32_t *chunk_e) {
+    for (int64_t col = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; col < k; col += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t a0 = colptrA[col], a1 = colptrA[col + 1];
+        if (a1 - a0 > LONG_COL) continue;
         const int64_t lb = (int64_t)rowptrB[col + 1] - rowptrB[col];
-        if (lb == 0) continue;
-        const int64_t s = F[col] + (e - colptrA[col]) * lb, r = s + lb;
-        for (int64_t c = ceil_div<int64_t>(s, chunk); c * chunk < r; ++c) chunk_e[c] = (c * chunk == s) ? (int32_t)e : (int32_t)(e + 1);
+        const int64_t s0 = F[col];
+        for (int32_t e = a0; e < a1; ++e) entry_info(e, s0 + (e - a0) * lb, lb, chunk, rowidxA, rowinfo, ainfo, chunk_e);
+    }
+}
+
+// One warp per listed long column.
+__global__ void k_entry_long(const int32_t *colptrA, const int32_t *rowidxA, const int32_t *rowptrB,
+                             const uint64_t *rowinfo, const int64_t *F, const int32_t *long_cols,
+                             const uint32_t *n_long, int64_t chunk, uint64_t *ainfo, int32_t *chunk_e) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t n = *n_long;
+    for (int64_t i = warp; i < n; i += nwarps) {
+        const int32_t col = long_cols[i];
+        const int32_t a0 = colptrA[col], a1 = colptrA[col + 1];
+        const int64_t lb = (int64_t)rowptrB[col + 1] - rowptrB[col];
+        const int64_t s0 = F[col];
+        for (int32_t e = a0 + lane; e < a1; e += 32) entry_info(e, s0 + (e - a0) * lb, lb, chunk, rowidxA, rowinfo, ainfo, chunk_e);
     }
 }
 
@@ -215,14 +245,14 @@ unsigned grid_for(int64_t n, int threads) {
 cudaError_t launch_symbolic(const SymbolicArgs &a, int64_t *scan_tmp, cudaStream_t s) {
     cudaError_t e;
     const int T = 256;
-    // 1. per-k flop and its prefix (Alg. 3); column of every A entry
+    // 1-2. per-k flop (Alg. 3), column of every A entry, per-row flop (Sec. III-B); prefixes
     if ((e = cudaMemsetAsync(a.n_long, 0, sizeof(uint32_t), s)) != cudaSuccess) return e;
-    k_flop_per_k<<<grid_for(a.k, T), T, 0, s>>>(a.k, a.colptrA, a.rowptrB, a.F, a.acol, a.long_cols, a.n_long);
-    k_acol_long<<<grid_for((int64_t)a.k * 32, T), T, 0, s>>>(a.colptrA, a.long_cols, a.n_long, a.acol);
-    if ((e = scan_i64(a.F, a.k, scan_tmp, s)) != cudaSuccess) return e;
-    // 2. per-row flop (Sec. III-B) and its prefix
     if ((e = cudaMemsetAsync(a.R, 0, sizeof(int64_t) * ((size_t)a.m + 1), s)) != cudaSuccess) return e;
-    k_row_flop<<<grid_for(a.nnzA, T), T, 0, s>>>(a.nnzA, a.acol, a.rowidxA, a.rowptrB, a.R);
+    k_flop_per_k<<<grid_for(a.k, T), T, 0, s>>>(a.k, a.colptrA, a.rowidxA, a.rowptrB, a.F, a.R, a.acol, a.long_cols,
+                                               a.n_long);
+    k_acol_long<<<grid_for((int64_t)a.k * 32, T), T, 0, s>>>(a.colptrA, a.rowidxA, a.rowptrB, a.long_cols, a.n_long,
+                                                            a.R, a.acol);
+    if ((e = scan_i64(a.F, a.k, scan_tmp, s)) != cudaSuccess) return e;
     if ((e = scan_i64(a.R, a.m, scan_tmp, s)) != cudaSuccess) return e;
     // 3. bins
     k_max_light<<<grid_for(a.m, T), T, 0, s>>>(a.m, a.R, a.heavy, a.hdr);
@@ -237,7 +267,7 @@ cudaError_t launch_symbolic(const SymbolicArgs &a, int64_t *scan_tmp, cudaStream
     k_bin_sizes<<<grid_for(a.m, T), T, 0, s>>>(a.R, a.bin_row, a.capacity, a.hdr, a.bin_off);
     if ((e = scan_i64(a.bin_off, a.m, scan_tmp, s)) != cudaSuccess) return e;
     k_finish_header<<<1, 1, 0, s>>>(a.F, a.k, a.m, a.R, a.bin_off, nullptr, nullptr, nullptr, a.hdr);
-    count_launches(9);  // the non-scan kernels above
+    count_launches(8);  // the non-scan kernels above
     return cudaGetLastError();
 }
 
@@ -277,9 +307,11 @@ cudaError_t launch_chunk_table(const SymbolicArgs &a, int64_t nchunks, int64_t c
     k_set_i32<<<1, 1, 0, s>>>(chunk_e + nchunks, (int32_t)a.nnzA);
     count_launches(1);
     if (a.nnzA > 0) {
-        k_entry_pass<<<grid_for(a.nnzA, 256), 256, 0, s>>>(a.nnzA, a.acol, a.rowidxA, a.rowinfo, a.F, a.colptrA,
-                                                           a.rowptrB, chunk, a.ainfo, chunk_e);
-        count_launches(1);
+        k_entry_pass<<<grid_for(a.k, 256), 256, 0, s>>>(a.k, a.colptrA, a.rowidxA, a.rowptrB, a.rowinfo, a.F, chunk,
+                                                        a.ainfo, chunk_e);
+        k_entry_long<<<grid_for((int64_t)a.k * 32, 256), 256, 0, s>>>(a.colptrA, a.rowidxA, a.rowptrB, a.rowinfo, a.F,
+                                                                      a.long_cols, a.n_long, chunk, a.ainfo, chunk_e);
+        count_launches(2);
     }
     return cudaGetLastError();
 }
