@@ -104,7 +104,9 @@ typedef struct pb_config {
     int64_t max_tuple_bytes; /* cap on the tuple workspace (tuples plus the global-sort scratch of
                                 oversize rows); a larger product runs in row panels, consecutive
                                 bin ranges processed one after another                            */
-    int64_t reserved1;
+    int64_t min_panels;      /* a product of at least min_panels * 2^20 tuples runs in about this many
+                                row panels even when its tuples fit (lets pb_spgemm_host copy a
+                                panel's rows of C back while the next panel computes); 0 or 1 = off */
 } pb_config;
 
 typedef struct pb_handle pb_handle;
@@ -161,6 +163,35 @@ pb_status pb_plan_query(const pb_plan *plan, int64_t *flop, int64_t *c_cap, size
  */
 pb_status pb_spgemm_numeric(pb_handle *h, const pb_plan *plan, const pb_csc *A, const pb_csr *B,
                             pb_csr_out *C, void *workspace, size_t ws_bytes, pb_stream_t stream);
+
+/*
+ * Product from and to HOST memory (the whole method, Alg. 3 then Alg. 2, with
+ * the host<->device copies overlapped with the kernels).  A and B hold host
+ * pointers (pinned memory gives full copy speed); C receives C = A * B in caller
+ * host buffers.  The library allocates device copies of A and B, the plan, the
+ * workspace and a flop-sized device C through the handle's allocator and frees
+ * them before returning.  Overlap: A's and B's value arrays and B's column
+ * indices are copied on a second stream while the symbolic phase runs; the
+ * numeric phase runs in row panels (cfg->min_panels, default 6 when 0) and each
+ * panel's rows of C are copied back as soon as its sort has finished, while the
+ * next panel computes.  Synchronous: returns when C is on the host.
+ *   C->cap     entries available in C->colidx / C->val (flop always suffices);
+ *              C->nnz receives nnz(C) (also when it exceeds cap)
+ *   *device_status  PB_OK, or PB_ERR_OVERFLOW when nnz(C) > C->cap (C incomplete),
+ *              or the device-detected error of the numeric phase.
+ * Errors (returned): INVALID_ARG, SHAPE, UNSUPPORTED_DTYPE, UNSUPPORTED, OOM, CUDA.
+ */
+typedef struct pb_csr_host {
+    int32_t nrows, ncols;
+    int64_t cap;
+    int64_t *rowptr;  /* host, nrows + 1 */
+    int32_t *colidx;  /* host, cap */
+    void *val;        /* host, cap values of the dtype's output type */
+    int64_t nnz;      /* output */
+} pb_csr_host;
+
+pb_status pb_spgemm_host(pb_handle *h, const pb_csc *A, const pb_csr *B, pb_dtype dtype, const pb_config *cfg,
+                         pb_csr_host *C, pb_stream_t stream, pb_status *device_status);
 
 /* Device-side status of the last numeric call made with this plan: PB_OK or
  * the first device-detected error.  Synchronises `stream` first. */

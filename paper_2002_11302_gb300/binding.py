@@ -55,7 +55,13 @@ class _CSROut(ctypes.Structure):
 class _Config(ctypes.Structure):
     _fields_ = [("bin_capacity", ctypes.c_int32), ("sort_threads", ctypes.c_int32),
                 ("expand_chunk", ctypes.c_int32), ("deterministic", ctypes.c_int32),
-                ("max_tuple_bytes", ctypes.c_int64), ("reserved1", ctypes.c_int64)]
+                ("max_tuple_bytes", ctypes.c_int64), ("min_panels", ctypes.c_int64)]
+
+
+class _CSRHost(ctypes.Structure):
+    _fields_ = [("nrows", ctypes.c_int32), ("ncols", ctypes.c_int32), ("cap", ctypes.c_int64),
+                ("rowptr", ctypes.c_void_p), ("colidx", ctypes.c_void_p), ("val", ctypes.c_void_p),
+                ("nnz", ctypes.c_int64)]
 
 
 class _BatchTune(ctypes.Structure):
@@ -91,6 +97,9 @@ SIGNATURES = {
     "pb_plan_destroy": (ctypes.c_int, [_VP]),
     "pb_set_phase_events": (ctypes.c_int, [_VP, _VP]),
     "pb_kernel_launches": (_I64, []),
+    "pb_spgemm_host": (ctypes.c_int, [_VP, ctypes.POINTER(_CSC), ctypes.POINTER(_CSR), ctypes.c_int,
+                                      ctypes.POINTER(_Config), ctypes.POINTER(_CSRHost), _VP,
+                                      ctypes.POINTER(ctypes.c_int)]),
     "pb_validate_operands": (ctypes.c_int, [_VP, ctypes.POINTER(_CSC), ctypes.POINTER(_CSR), _VP,
                                             ctypes.POINTER(ctypes.c_int)]),
     "pb_spgemm_noalloc": (ctypes.c_int, [ctypes.POINTER(_CSC), ctypes.POINTER(_CSR), ctypes.c_int,
@@ -265,8 +274,8 @@ def default_handle() -> Handle:
 
 
 def make_config(bin_capacity: int = 0, expand_chunk: int = 0, max_tuple_bytes: int = 0,
-                deterministic: bool = False) -> _Config:
-    return _Config(bin_capacity, 0, expand_chunk, 1 if deterministic else 0, max_tuple_bytes, 0)
+                deterministic: bool = False, min_panels: int = 0) -> _Config:
+    return _Config(bin_capacity, 0, expand_chunk, 1 if deterministic else 0, max_tuple_bytes, min_panels)
 
 
 class Plan:
@@ -621,3 +630,30 @@ def validate(A: CscMatrix, B: CsrMatrix, handle: Optional[Handle] = None, stream
     _check(h.lib, h.ptr, h.lib.pb_validate_operands(h.ptr, ctypes.byref(cA), ctypes.byref(cB), _stream_ptr(stream),
                                                     ctypes.byref(res)))
     return int(res.value), (h.lib.pb_last_error(h.ptr).decode() if res.value else "")
+
+
+def host_tensors(M, val_dtype=None, pin: bool = True):
+    """Host (optionally pinned) torch copies of a host CSC/CSR, for pb_spgemm_host."""
+    def t(a, dt=None):
+        x = torch.from_numpy(np.ascontiguousarray(a))
+        if dt is not None:
+            x = x.to(dt)
+        return x.pin_memory() if pin else x
+    if hasattr(M, "colptr"):
+        return CscMatrix(M.nrows, M.ncols, t(M.colptr, torch.int32), t(M.rowidx, torch.int32), t(M.val, val_dtype))
+    return CsrMatrix(M.nrows, M.ncols, t(M.rowptr, torch.int32), t(M.colidx, torch.int32), t(M.val, val_dtype))
+
+
+def spgemm_host(A: CscMatrix, B: CsrMatrix, C: CsrMatrix, dtype: int = PB_F64, config: Optional[_Config] = None,
+                handle: Optional[Handle] = None, stream=None):
+    """pb_spgemm_host: A, B and C in host memory (C preallocated: rowptr int64, colidx/val of any
+    capacity).  Returns (nnz, device_status)."""
+    h = handle or default_handle()
+    cA, cB = A._c(), B._c()
+    out = _CSRHost(A.nrows, B.ncols, int(C.colidx.numel()), C.rowptr.data_ptr(), C.colidx.data_ptr() or None,
+                   C.val.data_ptr() or None, 0)
+    dev = ctypes.c_int()
+    cfg = ctypes.byref(config) if config is not None else None
+    _check(h.lib, h.ptr, h.lib.pb_spgemm_host(h.ptr, ctypes.byref(cA), ctypes.byref(cB), dtype, cfg,
+                                              ctypes.byref(out), _stream_ptr(stream), ctypes.byref(dev)))
+    return int(out.nnz), int(dev.value)

@@ -365,8 +365,11 @@ pb_status pb_spgemm_symbolic(pb_handle *h, const pb_csc *A, const pb_csr *B, pb_
     // Row panels: with a tuple budget smaller than the whole product, bins are
     // grouped into consecutive panels whose tuples fit the budget together.
     const size_t per_tuple = 4 + tuple_val_bytes(dtype);
-    const int64_t budget = (cfg && cfg->max_tuple_bytes > 0) ? cfg->max_tuple_bytes / (int64_t)per_tuple : 0;
-    if (budget > 0 && p->hdr.tuples_padded > budget) {
+    int64_t budget = (cfg && cfg->max_tuple_bytes > 0) ? cfg->max_tuple_bytes / (int64_t)per_tuple : 0;
+    // min_panels: products of at least min_panels * 2^20 tuples are split into about that many panels
+    const int64_t want = (cfg && cfg->min_panels > 1) ? cfg->min_panels : 1;
+    const bool split_for_count = want > 1 && p->hdr.nbins >= want && p->hdr.tuples_padded >= (want << 20);
+    if ((budget > 0 && p->hdr.tuples_padded > budget) || split_for_count) {
         const size_t nb = (size_t)p->hdr.nbins, no = (size_t)p->hdr.n_oversize;
         std::vector<int64_t> off(nb + 1), obin(no), ochunk(no + 1), otup(no + 1);
         if ((e = cudaMemcpyAsync(off.data(), p->bin_off, 8 * (nb + 1), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
@@ -382,6 +385,17 @@ pb_status pb_spgemm_symbolic(pb_handle *h, const pb_csc *A, const pb_csr *B, pb_
         // an oversize bin also needs its size again in scratch for its global sort
         std::vector<char> is_over(nb, 0);
         for (int64_t ob : obin) is_over[ob] = 1;
+        if (split_for_count) {
+            int64_t total = 0, largest = 0;
+            for (size_t i = 0; i < nb; ++i) {
+                const int64_t c = (off[i + 1] - off[i]) * (is_over[i] ? 2 : 1);
+                total += c;
+                largest = c > largest ? c : largest;
+            }
+            int64_t even = ceil_div<int64_t>(total, want);
+            if (even < largest) even = largest;
+            if (budget <= 0 || even < budget) budget = even;
+        }
         int64_t b = 0;
         while (b < (int64_t)nb) {
             pb_panel pn{};
@@ -548,10 +562,12 @@ static OversizeArgs oversize_args(const pb_plan *p, void *workspace, const pb_pa
     return o;
 }
 
-pb_status pb_spgemm_numeric(pb_handle *h, const pb_plan *p, const pb_csc *A, const pb_csr *B, pb_csr_out *C,
-                            void *workspace, size_t ws_bytes, pb_stream_t stream_) {
-    if (!h || !p || !C) return PB_ERR_INVALID_ARG;
-    h->last_error.clear();
+// The numeric launch sequence; with panel_done, an event is recorded on the
+// stream after each panel's sort (pb_spgemm_host copies that panel's rows of C
+// back while the next panel computes).
+static pb_status run_numeric(pb_handle *h, const pb_plan *p, const pb_csc *A, const pb_csr *B, pb_csr_out *C,
+                             void *workspace, size_t ws_bytes, cudaStream_t s,
+                             const std::vector<cudaEvent_t> *panel_done) {
     NumericArgs a;
     pb_status st = fill_numeric(h, p, A, B, workspace, ws_bytes, a);
     if (st != PB_OK) return st;
@@ -562,7 +578,6 @@ pb_status pb_spgemm_numeric(pb_handle *h, const pb_plan *p, const pb_csc *A, con
     if (C->cap < 0 || (C->cap > 0 && (!C->colidx || !C->val)))
         return fail(h, PB_ERR_INVALID_ARG, "C arrays must not be NULL when cap > 0");
     a.count_only = count_only ? 1 : 0;
-    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream_);
     a.rowptr64 = C->rowptr64;
     a.rowptr32 = C->rowptr32;
     a.colidx = C->colidx;
@@ -584,7 +599,8 @@ pb_status pb_spgemm_numeric(pb_handle *h, const pb_plan *p, const pb_csc *A, con
     PB_CUDA(h, cudaMemsetAsync(w + p->ws_status, 0, 8 * nb, s));  // look-back words: all panels
     if (h->phase_on) PB_CUDA(h, cudaEventRecord(h->phase_ev[1], s));
     const bool single = p->panels.size() == 1;
-    for (const pb_panel &pn : p->panels) {
+    for (size_t i = 0; i < p->panels.size(); ++i) {
+        const pb_panel &pn = p->panels[i];
         // panels run one after another: the look-back chain continues across them
         a.bin_lo = pn.bin_lo;
         a.bin_hi = pn.bin_hi;
@@ -596,11 +612,145 @@ pb_status pb_spgemm_numeric(pb_handle *h, const pb_plan *p, const pb_csc *A, con
             PB_CUDA(h, launch_oversize(oversize_args(p, workspace, pn), p->over_passes, p->dtype, h->num_sms, s));
         if (h->phase_on && single) PB_CUDA(h, cudaEventRecord(h->phase_ev[2], s));
         PB_CUDA(h, launch_binsort(a, s));
+        if (panel_done) PB_CUDA(h, cudaEventRecord((*panel_done)[i], s));
     }
     if (h->phase_on) {
         if (!single) PB_CUDA(h, cudaEventRecord(h->phase_ev[2], s));
         PB_CUDA(h, cudaEventRecord(h->phase_ev[3], s));
     }
+    return PB_OK;
+}
+
+pb_status pb_spgemm_numeric(pb_handle *h, const pb_plan *p, const pb_csc *A, const pb_csr *B, pb_csr_out *C,
+                            void *workspace, size_t ws_bytes, pb_stream_t stream_) {
+    if (!h || !p || !C) return PB_ERR_INVALID_ARG;
+    h->last_error.clear();
+    return run_numeric(h, p, A, B, C, workspace, ws_bytes, reinterpret_cast<cudaStream_t>(stream_), nullptr);
+}
+
+// Device buffers of one pb_spgemm_host call, released on every exit path.
+struct HostCall {
+    pb_handle *h;
+    cudaStream_t s;
+    std::vector<std::pair<void *, size_t>> bufs;
+    std::vector<cudaEvent_t> events;
+    pb_plan *plan = nullptr;
+    void *get(size_t bytes) {
+        void *p = h->alloc(bytes ? bytes : 256, reinterpret_cast<pb_stream_t>(s), h->ctx);
+        if (p) bufs.push_back({p, bytes ? bytes : 256});
+        return p;
+    }
+    cudaEvent_t event() {
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return nullptr;
+        events.push_back(e);
+        return e;
+    }
+    ~HostCall() {
+        (void)cudaStreamSynchronize(s);
+        if (h->copy_stream) (void)cudaStreamSynchronize(h->copy_stream);
+        if (plan) pb_plan_destroy(plan);
+        for (auto &b : bufs) h->free_fn(b.first, b.second, reinterpret_cast<pb_stream_t>(s), h->ctx);
+        for (cudaEvent_t e : events) cudaEventDestroy(e);
+    }
+};
+
+pb_status pb_spgemm_host(pb_handle *h, const pb_csc *A, const pb_csr *B, pb_dtype dtype, const pb_config *cfg,
+                         pb_csr_host *C, pb_stream_t stream_, pb_status *device_status) {
+    if (!h || !C || !device_status) return PB_ERR_INVALID_ARG;
+    h->last_error.clear();
+    pb_status st = check_operands(h, A, B);
+    if (st != PB_OK) return st;
+    if (!valid_dtype(dtype)) return fail(h, PB_ERR_UNSUPPORTED_DTYPE, "unknown dtype");
+    if (C->nrows != A->nrows || C->ncols != B->ncols) return fail(h, PB_ERR_SHAPE, "C must be A.nrows x B.ncols");
+    if (!C->rowptr || C->cap < 0 || (C->cap > 0 && (!C->colidx || !C->val)))
+        return fail(h, PB_ERR_INVALID_ARG, "C host arrays");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream_);
+    if (!h->copy_stream) PB_CUDA(h, cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking));
+    if (!h->small_stream) PB_CUDA(h, cudaStreamCreateWithFlags(&h->small_stream, cudaStreamNonBlocking));
+    cudaStream_t sc = h->copy_stream, sr = h->small_stream;
+    HostCall call{h, s};
+    const size_t vin = dtype == PB_F32 ? 4 : 8, vout = vin;
+    const int32_t m = A->nrows, k = A->ncols, n = B->ncols;
+    // device copies of the operands; the value arrays go on the copy stream and
+    // overlap with the symbolic phase, which needs only the pointer and row-index arrays
+    int32_t *dcolptr = static_cast<int32_t *>(call.get(4 * ((size_t)k + 1)));
+    int32_t *drowidx = static_cast<int32_t *>(call.get(4 * (size_t)A->nnz));
+    void *dvalA = call.get(vin * (size_t)A->nnz);
+    int32_t *drowptr = static_cast<int32_t *>(call.get(4 * ((size_t)k + 1)));
+    int32_t *dcolidx = static_cast<int32_t *>(call.get(4 * (size_t)B->nnz));
+    void *dvalB = call.get(vin * (size_t)B->nnz);
+    if (!dcolptr || !drowidx || !dvalA || !drowptr || !dcolidx || !dvalB)
+        return fail(h, PB_ERR_OOM, "operand allocation failed");
+    cudaEvent_t ev_alloc = call.event(), ev_vals = call.event();
+    if (!ev_alloc || !ev_vals) return fail(h, PB_ERR_CUDA, "event creation failed");
+    PB_CUDA(h, cudaMemcpyAsync(dcolptr, A->colptr, 4 * ((size_t)k + 1), cudaMemcpyHostToDevice, s));
+    PB_CUDA(h, cudaMemcpyAsync(drowptr, B->rowptr, 4 * ((size_t)k + 1), cudaMemcpyHostToDevice, s));
+    if (A->nnz) PB_CUDA(h, cudaMemcpyAsync(drowidx, A->rowidx, 4 * (size_t)A->nnz, cudaMemcpyHostToDevice, s));
+    PB_CUDA(h, cudaEventRecord(ev_alloc, s));
+    PB_CUDA(h, cudaStreamWaitEvent(sc, ev_alloc, 0));
+    if (A->nnz) PB_CUDA(h, cudaMemcpyAsync(dvalA, A->val, vin * (size_t)A->nnz, cudaMemcpyHostToDevice, sc));
+    if (B->nnz) PB_CUDA(h, cudaMemcpyAsync(dcolidx, B->colidx, 4 * (size_t)B->nnz, cudaMemcpyHostToDevice, sc));
+    if (B->nnz) PB_CUDA(h, cudaMemcpyAsync(dvalB, B->val, vin * (size_t)B->nnz, cudaMemcpyHostToDevice, sc));
+    PB_CUDA(h, cudaEventRecord(ev_vals, sc));
+    const pb_csc dA{m, k, A->nnz, dcolptr, drowidx, dvalA};
+    const pb_csr dB{k, n, B->nnz, drowptr, dcolidx, dvalB};
+    pb_config c2{};
+    if (cfg) c2 = *cfg;
+    if (c2.min_panels == 0) c2.min_panels = 6;
+    st = pb_spgemm_symbolic(h, &dA, &dB, dtype, &c2, stream_, &call.plan);
+    if (st != PB_OK) {
+        call.plan = nullptr;
+        return st;
+    }
+    const pb_plan *p = call.plan;
+    const int64_t flop = p->hdr.flop;
+    const int64_t cap = flop > 0 ? flop : 1;
+    int64_t *drp = static_cast<int64_t *>(call.get(8 * ((size_t)m + 1)));
+    int32_t *dci = static_cast<int32_t *>(call.get(4 * (size_t)cap));
+    void *dva = call.get(vout * (size_t)cap);
+    void *ws = call.get(p->ws_bytes);
+    if (!drp || !dci || !dva || !ws) return fail(h, PB_ERR_OOM, "output or workspace allocation failed");
+    std::vector<cudaEvent_t> done(p->panels.size());
+    for (cudaEvent_t &e : done)
+        if (!(e = call.event())) return fail(h, PB_ERR_CUDA, "event creation failed");
+    PB_CUDA(h, cudaStreamWaitEvent(s, ev_vals, 0));
+    pb_csr_out dC{m, n, cap, drp, nullptr, dci, dva, nullptr};
+    st = run_numeric(h, p, &dA, &dB, &dC, ws, p->ws_bytes, s, &done);
+    if (st != PB_OK) return st;
+    // each panel's rows of C: [prefix before it, its last bin's inclusive prefix)
+    const uint64_t *status = reinterpret_cast<const uint64_t *>(static_cast<char *>(ws) + p->ws_status);
+    int64_t begin = 0;
+    bool overflow = false;
+    for (size_t i = 0; i < p->panels.size() && m > 0; ++i) {
+        const pb_panel &pn = p->panels[i];
+        uint64_t word = 0;
+        PB_CUDA(h, cudaStreamWaitEvent(sr, done[i], 0));
+        if (pn.bin_hi > pn.bin_lo) {
+            PB_CUDA(h, cudaMemcpyAsync(&word, status + (pn.bin_hi - 1), 8, cudaMemcpyDeviceToHost, sr));
+            PB_CUDA(h, cudaStreamSynchronize(sr));
+        }
+        const int64_t end = pn.bin_hi > pn.bin_lo ? (int64_t)(word & LB_VALUE_MASK) : begin;
+        if (end > C->cap) overflow = true;
+        if (!overflow && end > begin) {
+            PB_CUDA(h, cudaStreamWaitEvent(sc, done[i], 0));
+            PB_CUDA(h, cudaMemcpyAsync(C->colidx + begin, dci + begin, 4 * (size_t)(end - begin),
+                                       cudaMemcpyDeviceToHost, sc));
+            PB_CUDA(h, cudaMemcpyAsync(static_cast<char *>(C->val) + vout * (size_t)begin,
+                                       static_cast<char *>(dva) + vout * (size_t)begin, vout * (size_t)(end - begin),
+                                       cudaMemcpyDeviceToHost, sc));
+        }
+        begin = end;
+    }
+    if (!done.empty()) PB_CUDA(h, cudaStreamWaitEvent(sc, done.back(), 0));
+    PB_CUDA(h, cudaMemcpyAsync(C->rowptr, drp, 8 * ((size_t)m + 1), cudaMemcpyDeviceToHost, sc));
+    PB_CUDA(h, cudaStreamSynchronize(sc));
+    pb_status dev = PB_OK;
+    PB_CUDA(h, cudaStreamSynchronize(s));
+    st = pb_plan_status(p, stream_, &dev);
+    if (st != PB_OK) return st;
+    C->nnz = m > 0 ? begin : 0;
+    *device_status = overflow ? PB_ERR_OVERFLOW : dev;
     return PB_OK;
 }
 

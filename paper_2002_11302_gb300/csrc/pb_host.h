@@ -18,6 +18,13 @@ struct pb_handle {
     bool phase_on = false;
     // batched products: tuned parameters per (log2 n, d class) sparsity class
     std::vector<pb_batch_tune> tuning;
+    // pb_spgemm_host: streams for the bulk copies and for small reads (created on first use)
+    cudaStream_t copy_stream = nullptr;
+    cudaStream_t small_stream = nullptr;
+    ~pb_handle() {
+        if (copy_stream) cudaStreamDestroy(copy_stream);
+        if (small_stream) cudaStreamDestroy(small_stream);
+    }
 };
 
 namespace pb {
