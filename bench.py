@@ -775,6 +775,7 @@ def run_ours(args, w):
     total_ms = t_start.elapsed_time(t_end)
     for i in range(args.steps):
         phase_ms["symbolic"] += per_step[i][0].elapsed_time(per_step[i][1])
+    step_ms = [per_step[i][0].elapsed_time(per_step[i][2]) for i in range(args.steps)]
     total_ms, value = combine_replicas(total_ms, flop * args.steps, "cuda")
     ms_per_step = total_ms / args.steps
 
@@ -807,25 +808,60 @@ def run_ours(args, w):
                      "traffic": None if args.deterministic else stored_traffic(kname, w, flop),
                      "alg_bytes_per_launch": bytes_dom, "ms_per_launch": ms_dom},
         "pct_beta_ai": {"numeric": pct_numeric, "step": pct_step, "beta_gbs": hbm, "beta_kind": peak_kind,
-                        "ai_flop_per_byte": flop / by.total, "numeric_bytes": by.numeric, "step_bytes": by.total},
+                        "ai_flop_per_byte": flop / by.total, "numeric_bytes": by.numeric, "step_bytes": by.total,
+                        "numeric_vs_nominal_7900_gbs": by.numeric / (numeric_ms / 1e3) / 1e9 / 7900.0,
+                        # Tab. III with b = 16 bytes per element, as the paper counts
+                        "paper_b16_numeric": (16 * (A.nnz + B.nnz) + 32 * flop + 16 * nnz_c) / (numeric_ms / 1e3)
+                        / 1e9 / hbm},
+        "step_ms_stats": {"median": statistics.median(step_ms), "p10": float(np.percentile(step_ms, 10)),
+                          "p90": float(np.percentile(step_ms, 90)), "steps": len(step_ms)},
         "phases_ms": {k: v / args.steps for k, v in phase_ms.items()},
         "gflops_numeric": 2.0 * flop / (numeric_ms / 1e3) / 1e9,
         "gpu_launches": launches,
         "clocks": clocks,
     }
 
+    if dt == binding.PB_F64_F32TUPLE and rank == 0:
+        line["accuracy"] = f32_tuple_accuracy(A, B, C, nnz_c)
     if not args.no_e2e and not w.get("exact"):
         line["e2e"] = run_e2e(args, A, B, handle, torch, binding, flop)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
         t, cores, sflop, srows = cpu_oracle_run(A, B, repeats=3)
+        oracle.set_threads(1)
+        t1, _, sflop1, srows1 = cpu_oracle_run(A, B, repeats=1, budget_s=4.0)
+        oracle.set_threads(cores)
         line["cpu_baseline"] = {"value": 2.0 * sflop / t / 1e9, "unit": "GFLOPS", "cores": cores, "kind": "oracle",
                                 "sample": f"rows 0..{srows - 1} of {A.nrows} ({sflop} of {flop} multiplications), "
-                                          f"median of 3 runs"}
+                                          f"median of 3 runs",
+                                "one_thread": {"value": 2.0 * sflop1 / t1 / 1e9, "unit": "GFLOPS",
+                                               "sample": f"rows 0..{srows1 - 1} of {A.nrows}, one run"}}
     binding.set_phase_events(handle, None)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def f32_tuple_accuracy(A, B, C, nnz_c, budget_s: float = 3.0):
+    """Error of the FP32-tuple result against the FP64 oracle on a leading-row sample:
+    structure must be identical; values are reported as the largest relative error and
+    the largest error as a fraction of the bound 64 * 2^-24 * sum |a b|."""
+    import oracle
+    rows, _ = oracle_rows_for_budget(A, B, budget_s)
+    ref = oracle.spgemm(A, B, rows)
+    rp = C.rowptr.cpu().numpy()
+    last = int(rows[-1]) + 1
+    ci = C.colidx[: int(rp[last])].cpu().numpy()
+    va = C.val[: int(rp[last])].double().cpu().numpy()
+    same = np.array_equal(rp[: last + 1] - rp[0], ref.rowptr) and np.array_equal(ci, ref.colidx)
+    err = np.abs(va - ref.val)
+    rel = err / np.maximum(np.abs(ref.val), 1e-300)
+    bound = 64 * 2.0 ** -24 * ref.absval
+    return {"rows_sampled": int(last), "structure_identical": bool(same), "max_rel_err": float(rel.max(initial=0)),
+            "median_rel_err": float(np.median(rel)) if rel.size else 0.0,
+            "max_err_over_bound": float((err / np.maximum(bound, 1e-300)).max(initial=0)),
+            "reference": "FP64 oracle (Gustavson, ascending k)"}
 
 
 def run_e2e(args, A, B, handle, torch, binding, flop: int):

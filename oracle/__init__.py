@@ -56,6 +56,8 @@ def _load():
             f64p = ctypes.POINTER(ctypes.c_double)
             i32, i64 = ctypes.c_int32, ctypes.c_int64
             lib.pb_oracle_threads.restype = ctypes.c_int
+            lib.pb_oracle_set_threads.restype = None
+            lib.pb_oracle_set_threads.argtypes = [ctypes.c_int]
             lib.pb_oracle_flop.restype = i64
             lib.pb_oracle_flop.argtypes = [i32, i32p, i32p]
             lib.pb_oracle_row_flop.restype = None
@@ -89,6 +91,11 @@ def _f64(a):
 
 def threads() -> int:
     return int(_load().pb_oracle_threads())
+
+
+def set_threads(n: int) -> None:
+    """OpenMP threads of later oracle calls."""
+    _load().pb_oracle_set_threads(int(n))
 
 
 def _check(A, B):

@@ -42,6 +42,15 @@ int pb_oracle_threads(void) {
 #endif
 }
 
+/* Threads of later calls (for the one-thread timing of the CPU baseline). */
+void pb_oracle_set_threads(int n) {
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
 /* Alg. 3: total multiplications of the outer-product formulation. */
 int64_t pb_oracle_flop(int32_t k, const int32_t *colptrA, const int32_t *rowptrB) {
     int64_t flop = 0;
