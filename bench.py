@@ -694,7 +694,8 @@ def run_ours_serve(args, w):
                 "d2h_bytes_per_step": io["d2h"] / n_req, "p50_ms": pct(lat_e, 50), "p99_ms": pct(lat_e, 99),
                 "rate_rps": rates[1]},
     }
-    print(json.dumps(line), flush=True)
+    if int(os.environ.get("RANK", "0")) == 0:
+        print(json.dumps(line), flush=True)
 
 
 def run_ours(args, w):
