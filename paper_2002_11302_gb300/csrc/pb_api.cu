@@ -53,9 +53,10 @@ struct pb_plan {
     size_t over_map_bytes = 0;
     int32_t *over_chunk_bin = nullptr;
     int over_passes = 0;
+    int over_dense = 0, over_shift = 0;  // oversize rows merged in dense column tiles
     // workspace layout of the numeric phase
     size_t ws_keys = 0, ws_vals = 0, ws_cursor = 0, ws_status = 0, ws_ctrl = 0;
-    size_t ws_skeys = 0, ws_svals = 0, ws_hist = 0, ws_over_u = 0, ws_bytes = 0;
+    size_t ws_skeys = 0, ws_svals = 0, ws_hist = 0, ws_over_u = 0, ws_segcnt = 0, ws_overp = 0, ws_bytes = 0;
 };
 
 namespace {
@@ -318,6 +319,13 @@ pb_status pb_spgemm_symbolic(pb_handle *h, const pb_csc *A, const pb_csr *B, pb_
     // Oversize bins: work-item map for their global-memory radix sort.
     if (p->hdr.n_oversize > 0) {
         p->over_passes = (p->colbits + 7) / 8;
+        // Dense column tiles when the tuple and output value types agree (the merged
+        // sums are stored in the tuple slots) and order of sums need not be fixed.
+        const int shift = p->colbits > 8 ? p->colbits - 8 : 0;
+        p->over_dense = (dtype != PB_F64_F32TUPLE && !(cfg && cfg->deterministic) &&
+                         shift <= OVER_DENSE_MAX_SHIFT) ? 1 : 0;
+        p->over_shift = shift;
+        if (p->over_dense) p->over_passes = 1;  // the one partition pass leaves the tuples in scratch
         p->over_map_bytes = align256(4 * (size_t)p->hdr.over_chunks);
         p->over_map_mem = h->alloc(p->over_map_bytes, stream_, h->ctx);
         if (!p->over_map_mem) {
@@ -467,6 +475,12 @@ pb_status pb_spgemm_symbolic(pb_handle *h, const pb_csc *A, const pb_csr *B, pb_
     w += align256(4 * 256 * OC);
     p->ws_over_u = w;
     w += align256(8 * NO);
+    int64_t max_no = 0;
+    for (const pb_panel &pn : p->panels) max_no = std::max(max_no, pn.o_hi - pn.o_lo);
+    p->ws_segcnt = w;
+    w += align256(4 * 256 * (size_t)(p->over_dense ? max_no : 0));
+    p->ws_overp = w;
+    w += align256(8 * NO);
     p->ws_bytes = w;
     *out = p;
     return PB_OK;
@@ -532,6 +546,8 @@ static pb_status fill_numeric(pb_handle *h, const pb_plan *p, const pb_csc *A, c
     a.skeys = reinterpret_cast<uint32_t *>(w + p->ws_skeys);
     a.svals = w + p->ws_svals;
     a.over_passes = p->over_passes;
+    a.over_dense = p->over_dense;
+    a.over_p = reinterpret_cast<int64_t *>(w + p->ws_overp);
     return PB_OK;
 }
 
@@ -559,6 +575,10 @@ static OversizeArgs oversize_args(const pb_plan *p, void *workspace, const pb_pa
     o.svals = w + p->ws_svals;
     o.hist = reinterpret_cast<uint32_t *>(w + p->ws_hist);
     o.over_u = reinterpret_cast<int64_t *>(w + p->ws_over_u);
+    o.dense = p->over_dense;
+    o.dense_shift = p->over_shift;
+    o.seg_cnt = reinterpret_cast<int32_t *>(w + p->ws_segcnt);
+    o.over_p = reinterpret_cast<int64_t *>(w + p->ws_overp);
     return o;
 }
 
@@ -612,6 +632,12 @@ static pb_status run_numeric(pb_handle *h, const pb_plan *p, const pb_csc *A, co
             PB_CUDA(h, launch_oversize(oversize_args(p, workspace, pn), p->over_passes, p->dtype, h->num_sms, s));
         if (h->phase_on && single) PB_CUDA(h, cudaEventRecord(h->phase_ev[2], s));
         PB_CUDA(h, launch_binsort(a, s));
+        if (pn.o_hi > pn.o_lo && p->over_dense && !count_only) {
+            OversizeArgs o = oversize_args(p, workspace, pn);
+            o.colidxC = C->colidx;
+            o.valC = C->val;
+            PB_CUDA(h, launch_oversize_emit(o, p->dtype, h->num_sms, s));
+        }
         if (panel_done) PB_CUDA(h, cudaEventRecord((*panel_done)[i], s));
     }
     if (h->phase_on) {

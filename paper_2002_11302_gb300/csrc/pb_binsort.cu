@@ -319,6 +319,12 @@ __device__ void stream_oversize_bin(const NumericArgs &p, int64_t b, int32_t row
     const bool ok = *okp != 0;
     if (ok)
         for (int32_t r = row0 + tid; r < row1; r += THREADS) write_rowptr(p, r, r == row0 ? P : P + p.over_u[o]);
+    if (p.over_dense) {
+        // merged in dense tiles already: record where the row goes; a later kernel copies it
+        if (tid == 0) p.over_p[o] = ok ? P : -1;
+        __syncthreads();
+        return;
+    }
     int64_t running = 0;
     for (int64_t base = 0; base < N; base += THREADS) {
         const int64_t q = base + tid;

@@ -92,6 +92,15 @@ struct OversizeArgs {
     // [c_lo, c_hi); tuple offsets are relative to tuple_base (main buffer) and
     // over_base (scratch)
     int64_t o_lo, o_hi, c_lo, c_hi, tuple_base, over_base;
+    // dense tiles instead of the radix sort: one partition pass on the column's
+    // top digit (columns >> dense_shift), then per (row, tile) segment a dense
+    // accumulation over 2^dense_shift columns in shared memory
+    int dense;
+    int dense_shift;
+    int32_t *seg_cnt;   // [(o - o_lo) * 256 + digit] merged entries of each segment
+    int64_t *over_p;    // [n_over] C offset of each oversize row (-1: not written)
+    int32_t *colidxC;   // C, for the copy of the segments once the offsets are known
+    void *valC;
 };
 
 template <class T>
@@ -236,6 +245,11 @@ cudaError_t launch_chunk_table(const SymbolicArgs &a, int64_t nchunks, int64_t c
 cudaError_t launch_over_chunk_map(const int64_t *over_chunk_off, int64_t n_over, int32_t *over_chunk_bin,
                                   cudaStream_t s);
 cudaError_t launch_oversize(const OversizeArgs &a, int passes, int dtype, int num_sms, cudaStream_t s);
+// Dense mode: copy every oversize row's compacted segments to C at the offsets
+// the sort kernel recorded (after the sort kernel of the panel).
+cudaError_t launch_oversize_emit(const OversizeArgs &a, int dtype, int num_sms, cudaStream_t s);
+// Largest dense_shift (tile of 2^shift columns) the dense oversize path handles.
+constexpr int OVER_DENSE_MAX_SHIFT = 14;
 
 // ---------------------------------------------------------------------------
 // Batched products (pb_spgemm_batch).  The products are laid out back to back
@@ -318,6 +332,8 @@ struct NumericArgs {
     uint32_t *skeys;
     void *svals;
     int over_passes;
+    int over_dense;     // oversize rows were accumulated in dense tiles: publish only
+    int64_t *over_p;    // [n_over] C offset of each oversize row, written by the sort kernel
     // deterministic mode: the first tuple position of each A entry's run (null: atomic cursors)
     const int64_t *apos;
     // batched products (null for a single product)

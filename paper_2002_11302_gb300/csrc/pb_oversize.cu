@@ -53,9 +53,8 @@ __device__ inline void pass_buffers(const OversizeArgs &a, int pass, const Chunk
 }
 
 template <class TV>
-__global__ void __launch_bounds__(OT) k_over_hist(const OversizeArgs a, int pass) {
+__global__ void __launch_bounds__(OT) k_over_hist(const OversizeArgs a, int pass, int shift) {
     __shared__ uint32_t h[256];
-    const int shift = 8 * pass;
     for (int64_t c = a.c_lo + blockIdx.x; c < a.c_hi; c += gridDim.x) {
         const ChunkRef r = chunk_ref(a, c);
         const uint32_t *sk;
@@ -93,10 +92,9 @@ __global__ void __launch_bounds__(256) k_over_offsets(const OversizeArgs a) {
 }
 
 template <class TV>
-__global__ void __launch_bounds__(OT) k_over_scatter(const OversizeArgs a, int pass) {
+__global__ void __launch_bounds__(OT) k_over_scatter(const OversizeArgs a, int pass, int shift) {
     __shared__ uint32_t wc[256 * ONW];  // per (digit, warp) counts, then in-chunk offsets
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int shift = 8 * pass;
     for (int64_t c = a.c_lo + blockIdx.x; c < a.c_hi; c += gridDim.x) {
         const ChunkRef r = chunk_ref(a, c);
         const uint32_t *sk;
@@ -176,6 +174,139 @@ __global__ void __launch_bounds__(OT) k_over_heads(const OversizeArgs a, int pas
     }
 }
 
+
+// ---------------------------------------------------------------------------
+// Dense tiles for oversize rows.  After one partition pass on the column's top
+// digit (column >> dense_shift), the tuples of oversize row o with digit d form
+// one contiguous segment of the scratch buffer.  A CTA sums the segment into a
+// dense shared-memory tile of 2^dense_shift FP64 accumulators with a presence
+// bitmap (every structural entry is kept, exact-zero sums included), then
+// writes the merged entries back over the segment's start in column order:
+// the concatenation of a row's segments in digit order is its merged, sorted
+// row (Sec. III-E) without a sort.  Order of the sums within a column is not
+// fixed (shared-memory atomics), so deterministic mode keeps the radix sort.
+// ---------------------------------------------------------------------------
+constexpr int DT = 256;  // threads per CTA of the dense kernels
+
+__device__ inline void segment_range(const OversizeArgs &a, int64_t o, int d, int64_t *start, int64_t *end) {
+    const int64_t bin = a.over_bin[o];
+    const int64_t N = a.R[a.bin_row[bin + 1]] - a.R[a.bin_row[bin]];
+    const int64_t c0 = a.over_chunk_off[o] - a.c_lo;  // the bin's first work item: digit offsets of the bin
+    *start = a.hist[c0 * 256 + d];
+    *end = d < 255 ? (int64_t)a.hist[c0 * 256 + d + 1] : N;
+}
+
+template <class TV>
+__global__ void __launch_bounds__(DT) k_over_dense(const OversizeArgs a) {
+    extern __shared__ __align__(16) unsigned char sraw[];
+    const int w = a.dense_shift;
+    const int W = 1 << w, NWD = (W + 31) / 32;
+    double *acc = reinterpret_cast<double *>(sraw);
+    uint32_t *bm = reinterpret_cast<uint32_t *>(acc + W);
+    int64_t *scratch = reinterpret_cast<int64_t *>(bm + ((NWD + 1) & ~1));
+    const int tid = threadIdx.x;
+    for (int i = tid; i < W; i += DT) acc[i] = 0.0;
+    for (int i = tid; i < NWD; i += DT) bm[i] = 0;
+    __syncthreads();
+    const int per = (NWD + DT - 1) / DT;  // bitmap words per thread in the compaction
+    const int64_t nitems = (a.o_hi - a.o_lo) * 256;
+    for (int64_t item = blockIdx.x; item < nitems; item += gridDim.x) {
+        const int64_t o = a.o_lo + item / 256;
+        const int d = (int)(item % 256);
+        int64_t start, end;
+        segment_range(a, o, d, &start, &end);
+        int32_t *slot = a.seg_cnt + (o - a.o_lo) * 256 + d;
+        if (start >= end) {
+            if (tid == 0) *slot = 0;
+            continue;
+        }
+        uint32_t *xk = a.skeys + (a.over_tuple_off[o] - a.over_base);
+        TV *xv = static_cast<TV *>(a.svals) + (a.over_tuple_off[o] - a.over_base);
+        for (int64_t q = start + tid; q < end; q += DT) {
+            const uint32_t loc = xk[q] & (uint32_t)(W - 1);
+            atomicAdd(&acc[loc], (double)xv[q]);
+            atomicOr(&bm[loc >> 5], 1u << (loc & 31));
+        }
+        __syncthreads();
+        uint32_t c = 0;
+        for (int j = 0; j < per; ++j) {
+            const int wi = tid * per + j;
+            if (wi < NWD) c += __popc(bm[wi]);
+        }
+        int64_t total;
+        int64_t pos = start + block_exclusive_scan<int64_t, DT>((int64_t)c, scratch, &total);
+        const uint32_t base = (uint32_t)d << w;
+        for (int j = 0; j < per; ++j) {
+            const int wi = tid * per + j;
+            if (wi >= NWD) break;
+            uint32_t m = bm[wi];
+            bm[wi] = 0;
+            while (m) {
+                const int b = __ffs(m) - 1;
+                m &= m - 1;
+                const int loc = wi * 32 + b;
+                xk[pos] = base | (uint32_t)loc;
+                xv[pos] = (TV)acc[loc];
+                acc[loc] = 0.0;
+                ++pos;
+            }
+        }
+        __syncthreads();
+        if (tid == 0) {
+            *slot = (int32_t)total;
+            if (total) atomicAdd(reinterpret_cast<unsigned long long *>(&a.over_u[o]), (unsigned long long)total);
+        }
+    }
+}
+
+template <class TV>
+cudaError_t run_dense(const OversizeArgs &a, int num_sms, cudaStream_t s) {
+    const int W = 1 << a.dense_shift, NWD = (W + 31) / 32;
+    const size_t smem = 8 * (size_t)W + 4 * (size_t)((NWD + 1) & ~1) + 8 * 40;
+    auto kern = k_over_dense<TV>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, DT, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    int64_t grid = (int64_t)num_sms * per_sm;
+    const int64_t items = (a.o_hi - a.o_lo) * 256;
+    if (grid > items) grid = items;
+    if (grid < 1) return cudaSuccess;
+    kern<<<(unsigned)grid, DT, smem, s>>>(a);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+// Copy each segment's merged entries to C: row offset (recorded by the sort
+// kernel) plus the merged entries of the row's earlier segments.
+template <class TV, class OV>
+__global__ void __launch_bounds__(DT) k_over_emit(const OversizeArgs a) {
+    __shared__ int64_t scratch[40];
+    const int tid = threadIdx.x;
+    OV *valC = static_cast<OV *>(a.valC);
+    const int64_t nitems = (a.o_hi - a.o_lo) * 256;
+    for (int64_t item = blockIdx.x; item < nitems; item += gridDim.x) {
+        const int64_t o = a.o_lo + item / 256;
+        const int d = (int)(item % 256);
+        const int64_t P = a.over_p[o];
+        const int32_t *cnt = a.seg_cnt + (o - a.o_lo) * 256;
+        const int32_t n = cnt[d];
+        if (P < 0 || n == 0) continue;
+        const int64_t before = block_reduce_sum<int64_t, DT>(tid < d ? (int64_t)cnt[tid] : 0, scratch);
+        int64_t start, end;
+        segment_range(a, o, d, &start, &end);
+        const uint32_t *xk = a.skeys + (a.over_tuple_off[o] - a.over_base) + start;
+        const TV *xv = static_cast<const TV *>(a.svals) + (a.over_tuple_off[o] - a.over_base) + start;
+        const int64_t out = P + before;
+        for (int i = tid; i < n; i += DT) {
+            a.colidxC[out + i] = (int32_t)xk[i];
+            valC[out + i] = (OV)xv[i];
+        }
+    }
+}
+
 template <class TV>
 cudaError_t run_oversize(const OversizeArgs &a, int passes, int num_sms, cudaStream_t s) {
     const int64_t g4 = (int64_t)num_sms * 4, g8 = (int64_t)num_sms * 8;
@@ -184,10 +315,18 @@ cudaError_t run_oversize(const OversizeArgs &a, int passes, int num_sms, cudaStr
     const unsigned ogrid = (unsigned)(no < g8 ? no : g8);
     cudaError_t e = cudaMemsetAsync(a.over_u + a.o_lo, 0, 8 * (size_t)no, s);
     if (e != cudaSuccess) return e;
-    for (int pass = 0; pass < passes; ++pass) {
-        k_over_hist<TV><<<grid, OT, 0, s>>>(a, pass);
+    if (a.dense) {
+        // one partition pass on the top digit, then dense accumulation per segment
+        k_over_hist<TV><<<grid, OT, 0, s>>>(a, 0, a.dense_shift);
         k_over_offsets<<<ogrid, 256, 0, s>>>(a);
-        k_over_scatter<TV><<<grid, OT, 0, s>>>(a, pass);
+        k_over_scatter<TV><<<grid, OT, 0, s>>>(a, 0, a.dense_shift);
+        count_launches(3);
+        return run_dense<TV>(a, num_sms, s);
+    }
+    for (int pass = 0; pass < passes; ++pass) {
+        k_over_hist<TV><<<grid, OT, 0, s>>>(a, pass, 8 * pass);
+        k_over_offsets<<<ogrid, 256, 0, s>>>(a);
+        k_over_scatter<TV><<<grid, OT, 0, s>>>(a, pass, 8 * pass);
         count_launches(3);
     }
     k_over_heads<<<grid, OT, 0, s>>>(a, passes);
@@ -201,6 +340,20 @@ cudaError_t launch_oversize(const OversizeArgs &a, int passes, int dtype, int nu
     if (a.o_hi <= a.o_lo) return cudaSuccess;
     if (dtype == PB_F64) return run_oversize<double>(a, passes, num_sms, s);
     return run_oversize<float>(a, passes, num_sms, s);
+}
+
+cudaError_t launch_oversize_emit(const OversizeArgs &a, int dtype, int num_sms, cudaStream_t s) {
+    if (a.o_hi <= a.o_lo || !a.dense) return cudaSuccess;
+    const int64_t items = (a.o_hi - a.o_lo) * 256;
+    int64_t grid = (int64_t)num_sms * 8;
+    if (grid > items) grid = items;
+    switch (dtype) {
+        case PB_F64: k_over_emit<double, double><<<(unsigned)grid, DT, 0, s>>>(a); break;
+        case PB_F32: k_over_emit<float, float><<<(unsigned)grid, DT, 0, s>>>(a); break;
+        default: return cudaErrorInvalidValue;  // dense mode needs tuple and output types alike
+    }
+    count_launches(1);
+    return cudaGetLastError();
 }
 
 }  // namespace pb

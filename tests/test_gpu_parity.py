@@ -64,6 +64,30 @@ def test_rmat_small_skewed(pb):
     assert_matches(C, oracle.spgemm(A, B), EPS["f64"])
 
 
+def test_oversize_rows_dense_tiles(pb):
+    """Hub rows above the bin capacity are merged in dense column tiles: structure exact
+    (including exact-zero sums: all-zero values keep every structural entry), FP64 and FP32."""
+    A, B = synth.rmat(12, 8, seed=41)
+    assert int(np.max(oracle.row_flop(A, B))) > 4096
+    ref = oracle.spgemm(A, B)
+    assert_matches(run(pb, A, B), ref, EPS["f64"])
+    A32 = synth.CSC(A.nrows, A.ncols, A.colptr, A.rowidx, A.val.astype(np.float32))
+    B32 = synth.CSR(B.nrows, B.ncols, B.rowptr, B.colidx, B.val.astype(np.float32))
+    assert_matches(run(pb, A32, B32, dtype=1, vdt=torch.float32), oracle.spgemm(A32, B32), EPS["f32"])
+    Az = synth.CSC(A.nrows, A.ncols, A.colptr, A.rowidx, np.zeros_like(A.val))
+    Bz = synth.CSR(B.nrows, B.ncols, B.rowptr, B.colidx, np.zeros_like(B.val))
+    C = run(pb, Az, Bz)
+    assert np.array_equal(C.rowptr.cpu().numpy(), ref.rowptr)
+    assert np.array_equal(C.colidx.cpu().numpy(), ref.colidx)
+    assert not np.any(C.val.cpu().numpy())
+
+
+def test_oversize_rows_counting_run_then_exact_c(pb):
+    A, B = synth.rmat(12, 8, seed=42)
+    C, plan = pb.spgemm_exact(pb.csc_to_device(A), pb.csr_to_device(B))
+    assert_matches(C, oracle.spgemm(A, B), EPS["f64"])
+
+
 def test_identity_and_permutation_bit_exact(pb):
     A, B = synth.er(5000, 6, seed=3)
     Ic, Ir = synth.identity(5000)
