@@ -200,15 +200,17 @@ template <class TV>
 __global__ void __launch_bounds__(DT) k_over_dense(const OversizeArgs a) {
     extern __shared__ __align__(16) unsigned char sraw[];
     const int w = a.dense_shift;
-    const int W = 1 << w, NWD = (W + 31) / 32;
+    const int W = 1 << w;
     double *acc = reinterpret_cast<double *>(sraw);
-    uint32_t *bm = reinterpret_cast<uint32_t *>(acc + W);
-    int64_t *scratch = reinterpret_cast<int64_t *>(bm + ((NWD + 1) & ~1));
+    uint8_t *seen = reinterpret_cast<uint8_t *>(acc + W);  // presence of each column of the tile
+    int64_t *scratch = reinterpret_cast<int64_t *>(seen + ((W + 15) & ~15));
     const int tid = threadIdx.x;
-    for (int i = tid; i < W; i += DT) acc[i] = 0.0;
-    for (int i = tid; i < NWD; i += DT) bm[i] = 0;
+    for (int i = tid; i < W; i += DT) {
+        acc[i] = 0.0;
+        seen[i] = 0;
+    }
     __syncthreads();
-    const int per = (NWD + DT - 1) / DT;  // bitmap words per thread in the compaction
+    const int per = (W + DT - 1) / DT;  // tile columns per thread in the compaction (contiguous)
     const int64_t nitems = (a.o_hi - a.o_lo) * 256;
     for (int64_t item = blockIdx.x; item < nitems; item += gridDim.x) {
         const int64_t o = a.o_lo + item / 256;
@@ -225,31 +227,22 @@ __global__ void __launch_bounds__(DT) k_over_dense(const OversizeArgs a) {
         for (int64_t q = start + tid; q < end; q += DT) {
             const uint32_t loc = xk[q] & (uint32_t)(W - 1);
             atomicAdd(&acc[loc], (double)xv[q]);
-            atomicOr(&bm[loc >> 5], 1u << (loc & 31));
+            seen[loc] = 1;  // every writer stores the same value
         }
         __syncthreads();
+        const int c0 = tid * per, c1 = min(c0 + per, W);
         uint32_t c = 0;
-        for (int j = 0; j < per; ++j) {
-            const int wi = tid * per + j;
-            if (wi < NWD) c += __popc(bm[wi]);
-        }
+        for (int i = c0; i < c1; ++i) c += seen[i];
         int64_t total;
         int64_t pos = start + block_exclusive_scan<int64_t, DT>((int64_t)c, scratch, &total);
         const uint32_t base = (uint32_t)d << w;
-        for (int j = 0; j < per; ++j) {
-            const int wi = tid * per + j;
-            if (wi >= NWD) break;
-            uint32_t m = bm[wi];
-            bm[wi] = 0;
-            while (m) {
-                const int b = __ffs(m) - 1;
-                m &= m - 1;
-                const int loc = wi * 32 + b;
-                xk[pos] = base | (uint32_t)loc;
-                xv[pos] = (TV)acc[loc];
-                acc[loc] = 0.0;
-                ++pos;
-            }
+        for (int i = c0; i < c1; ++i) {
+            if (!seen[i]) continue;
+            xk[pos] = base | (uint32_t)i;
+            xv[pos] = (TV)acc[i];
+            acc[i] = 0.0;
+            seen[i] = 0;
+            ++pos;
         }
         __syncthreads();
         if (tid == 0) {
@@ -259,10 +252,24 @@ __global__ void __launch_bounds__(DT) k_over_dense(const OversizeArgs a) {
     }
 }
 
+// Per oversize row: the merged-entry counts of its 256 segments become their
+// exclusive prefixes (the segments' offsets inside the row's part of C).
+__global__ void __launch_bounds__(256) k_over_segscan(const OversizeArgs a) {
+    __shared__ int64_t scratch[40];
+    for (int64_t o = a.o_lo + blockIdx.x; o < a.o_hi; o += gridDim.x) {
+        int32_t *cnt = a.seg_cnt + (o - a.o_lo) * 256;
+        const int64_t v = cnt[threadIdx.x];
+        int64_t total;
+        const int64_t pre = block_exclusive_scan<int64_t, 256>(v, scratch, &total);
+        cnt[threadIdx.x] = (int32_t)pre;
+        __syncthreads();
+    }
+}
+
 template <class TV>
 cudaError_t run_dense(const OversizeArgs &a, int num_sms, cudaStream_t s) {
-    const int W = 1 << a.dense_shift, NWD = (W + 31) / 32;
-    const size_t smem = 8 * (size_t)W + 4 * (size_t)((NWD + 1) & ~1) + 8 * 40;
+    const int W = 1 << a.dense_shift;
+    const size_t smem = 8 * (size_t)W + (size_t)((W + 15) & ~15) + 8 * 40;
     auto kern = k_over_dense<TV>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -275,38 +282,39 @@ cudaError_t run_dense(const OversizeArgs &a, int num_sms, cudaStream_t s) {
     if (grid > items) grid = items;
     if (grid < 1) return cudaSuccess;
     kern<<<(unsigned)grid, DT, smem, s>>>(a);
-    count_launches(1);
+    const int64_t no = a.o_hi - a.o_lo;
+    k_over_segscan<<<(unsigned)(no < (int64_t)num_sms * 8 ? no : (int64_t)num_sms * 8), 256, 0, s>>>(a);
+    count_launches(2);
     return cudaGetLastError();
 }
 
-// Copy each segment's merged entries to C: row offset (recorded by the sort
-// kernel) plus the merged entries of the row's earlier segments.
+// Copy each segment's merged entries to C at the row offset (recorded by the
+// sort kernel) plus the segment's offset inside the row; one warp per segment.
 template <class TV, class OV>
-__global__ void __launch_bounds__(DT) k_over_emit(const OversizeArgs a) {
-    __shared__ int64_t scratch[40];
-    const int tid = threadIdx.x;
+__global__ void __launch_bounds__(256) k_over_emit(const OversizeArgs a) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     OV *valC = static_cast<OV *>(a.valC);
     const int64_t nitems = (a.o_hi - a.o_lo) * 256;
-    for (int64_t item = blockIdx.x; item < nitems; item += gridDim.x) {
+    for (int64_t item = warp; item < nitems; item += nwarps) {
         const int64_t o = a.o_lo + item / 256;
         const int d = (int)(item % 256);
         const int64_t P = a.over_p[o];
-        const int32_t *cnt = a.seg_cnt + (o - a.o_lo) * 256;
-        const int32_t n = cnt[d];
-        if (P < 0 || n == 0) continue;
-        const int64_t before = block_reduce_sum<int64_t, DT>(tid < d ? (int64_t)cnt[tid] : 0, scratch);
+        if (P < 0) continue;
+        const int32_t *off = a.seg_cnt + (o - a.o_lo) * 256;
+        const int64_t lo = off[d], hi = d < 255 ? (int64_t)off[d + 1] : a.over_u[o];
+        if (hi <= lo) continue;
         int64_t start, end;
         segment_range(a, o, d, &start, &end);
         const uint32_t *xk = a.skeys + (a.over_tuple_off[o] - a.over_base) + start;
         const TV *xv = static_cast<const TV *>(a.svals) + (a.over_tuple_off[o] - a.over_base) + start;
-        const int64_t out = P + before;
-        for (int i = tid; i < n; i += DT) {
-            a.colidxC[out + i] = (int32_t)xk[i];
-            valC[out + i] = (OV)xv[i];
+        for (int64_t i = lane; i < hi - lo; i += 32) {
+            a.colidxC[P + lo + i] = (int32_t)xk[i];
+            valC[P + lo + i] = (OV)xv[i];
         }
     }
 }
-
 template <class TV>
 cudaError_t run_oversize(const OversizeArgs &a, int passes, int num_sms, cudaStream_t s) {
     const int64_t g4 = (int64_t)num_sms * 4, g8 = (int64_t)num_sms * 8;
@@ -346,10 +354,10 @@ cudaError_t launch_oversize_emit(const OversizeArgs &a, int dtype, int num_sms, 
     if (a.o_hi <= a.o_lo || !a.dense) return cudaSuccess;
     const int64_t items = (a.o_hi - a.o_lo) * 256;
     int64_t grid = (int64_t)num_sms * 8;
-    if (grid > items) grid = items;
+    if (grid > ceil_div<int64_t>(items, 8)) grid = ceil_div<int64_t>(items, 8);
     switch (dtype) {
-        case PB_F64: k_over_emit<double, double><<<(unsigned)grid, DT, 0, s>>>(a); break;
-        case PB_F32: k_over_emit<float, float><<<(unsigned)grid, DT, 0, s>>>(a); break;
+        case PB_F64: k_over_emit<double, double><<<(unsigned)grid, 256, 0, s>>>(a); break;
+        case PB_F32: k_over_emit<float, float><<<(unsigned)grid, 256, 0, s>>>(a); break;
         default: return cudaErrorInvalidValue;  // dense mode needs tuple and output types alike
     }
     count_launches(1);
