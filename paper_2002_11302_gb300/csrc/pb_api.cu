@@ -56,7 +56,7 @@ struct pb_plan {
     int over_dense = 0, over_shift = 0;  // oversize rows merged in dense column tiles
     // workspace layout of the numeric phase
     size_t ws_keys = 0, ws_vals = 0, ws_cursor = 0, ws_status = 0, ws_ctrl = 0;
-    size_t ws_skeys = 0, ws_svals = 0, ws_hist = 0, ws_over_u = 0, ws_segcnt = 0, ws_overp = 0, ws_bytes = 0;
+    size_t ws_skeys = 0, ws_svals = 0, ws_hist = 0, ws_over_u = 0, ws_overp = 0, ws_bytes = 0;
 };
 
 namespace {
@@ -475,10 +475,6 @@ pb_status pb_spgemm_symbolic(pb_handle *h, const pb_csc *A, const pb_csr *B, pb_
     w += align256(4 * 256 * OC);
     p->ws_over_u = w;
     w += align256(8 * NO);
-    int64_t max_no = 0;
-    for (const pb_panel &pn : p->panels) max_no = std::max(max_no, pn.o_hi - pn.o_lo);
-    p->ws_segcnt = w;
-    w += align256(4 * 256 * (size_t)(p->over_dense ? max_no : 0));
     p->ws_overp = w;
     w += align256(8 * NO);
     p->ws_bytes = w;
@@ -577,7 +573,6 @@ static OversizeArgs oversize_args(const pb_plan *p, void *workspace, const pb_pa
     o.over_u = reinterpret_cast<int64_t *>(w + p->ws_over_u);
     o.dense = p->over_dense;
     o.dense_shift = p->over_shift;
-    o.seg_cnt = reinterpret_cast<int32_t *>(w + p->ws_segcnt);
     o.over_p = reinterpret_cast<int64_t *>(w + p->ws_overp);
     return o;
 }

@@ -93,11 +93,10 @@ struct OversizeArgs {
     // over_base (scratch)
     int64_t o_lo, o_hi, c_lo, c_hi, tuple_base, over_base;
     // dense tiles instead of the radix sort: one partition pass on the column's
-    // top digit (columns >> dense_shift), then per (row, tile) segment a dense
-    // accumulation over 2^dense_shift columns in shared memory
+    // top digit (columns >> dense_shift), then per row a dense accumulation of
+    // each tile of 2^dense_shift columns in shared memory
     int dense;
     int dense_shift;
-    int32_t *seg_cnt;   // [(o - o_lo) * 256 + digit] merged entries of each segment
     int64_t *over_p;    // [n_over] C offset of each oversize row (-1: not written)
     int32_t *colidxC;   // C, for the copy of the segments once the offsets are known
     void *valC;

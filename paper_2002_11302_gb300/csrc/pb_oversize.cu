@@ -177,24 +177,17 @@ __global__ void __launch_bounds__(OT) k_over_heads(const OversizeArgs a, int pas
 
 // ---------------------------------------------------------------------------
 // Dense tiles for oversize rows.  After one partition pass on the column's top
-// digit (column >> dense_shift), the tuples of oversize row o with digit d form
-// one contiguous segment of the scratch buffer.  A CTA sums the segment into a
-// dense shared-memory tile of 2^dense_shift FP64 accumulators with a presence
-// bitmap (every structural entry is kept, exact-zero sums included), then
-// writes the merged entries back over the segment's start in column order:
-// the concatenation of a row's segments in digit order is its merged, sorted
-// row (Sec. III-E) without a sort.  Order of the sums within a column is not
+// digit (column >> dense_shift), the tuples of an oversize row with digit d form
+// one contiguous segment of the scratch buffer.  One CTA per row walks its
+// segments in digit order; it sums each into a dense shared-memory tile of
+// 2^dense_shift FP64 accumulators with presence flags (every structural entry
+// is kept, exact-zero sums included) and writes the merged entries back in
+// column order right after those of the previous segments.  The row's merged,
+// sorted entries (Sec. III-E) thus end up contiguous at the start of its
+// scratch region without a sort.  The order of the sums within a column is not
 // fixed (shared-memory atomics), so deterministic mode keeps the radix sort.
 // ---------------------------------------------------------------------------
 constexpr int DT = 256;  // threads per CTA of the dense kernels
-
-__device__ inline void segment_range(const OversizeArgs &a, int64_t o, int d, int64_t *start, int64_t *end) {
-    const int64_t bin = a.over_bin[o];
-    const int64_t N = a.R[a.bin_row[bin + 1]] - a.R[a.bin_row[bin]];
-    const int64_t c0 = a.over_chunk_off[o] - a.c_lo;  // the bin's first work item: digit offsets of the bin
-    *start = a.hist[c0 * 256 + d];
-    *end = d < 255 ? (int64_t)a.hist[c0 * 256 + d + 1] : N;
-}
 
 template <class TV>
 __global__ void __launch_bounds__(DT) k_over_dense(const OversizeArgs a) {
@@ -202,74 +195,60 @@ __global__ void __launch_bounds__(DT) k_over_dense(const OversizeArgs a) {
     const int w = a.dense_shift;
     const int W = 1 << w;
     double *acc = reinterpret_cast<double *>(sraw);
-    uint8_t *seen = reinterpret_cast<uint8_t *>(acc + W);  // presence of each column of the tile
-    int64_t *scratch = reinterpret_cast<int64_t *>(seen + ((W + 15) & ~15));
+    int64_t *offs = reinterpret_cast<int64_t *>(acc + W);           // [257] segment starts of the row
+    int64_t *scratch = offs + 264;
+    uint8_t *seen = reinterpret_cast<uint8_t *>(scratch + 40);       // presence of each column of the tile
     const int tid = threadIdx.x;
     for (int i = tid; i < W; i += DT) {
         acc[i] = 0.0;
         seen[i] = 0;
     }
-    __syncthreads();
     const int per = (W + DT - 1) / DT;  // tile columns per thread in the compaction (contiguous)
-    const int64_t nitems = (a.o_hi - a.o_lo) * 256;
-    for (int64_t item = blockIdx.x; item < nitems; item += gridDim.x) {
-        const int64_t o = a.o_lo + item / 256;
-        const int d = (int)(item % 256);
-        int64_t start, end;
-        segment_range(a, o, d, &start, &end);
-        int32_t *slot = a.seg_cnt + (o - a.o_lo) * 256 + d;
-        if (start >= end) {
-            if (tid == 0) *slot = 0;
-            continue;
-        }
+    const int c0t = tid * per, c1t = min(c0t + per, W);
+    for (int64_t o = a.o_lo + blockIdx.x; o < a.o_hi; o += gridDim.x) {
+        const int64_t bin = a.over_bin[o];
+        const int64_t N = a.R[a.bin_row[bin + 1]] - a.R[a.bin_row[bin]];
+        const int64_t c0 = a.over_chunk_off[o] - a.c_lo;  // the bin's first work item holds its digit offsets
+        offs[tid] = a.hist[c0 * 256 + tid];
+        if (tid == 0) offs[256] = N;
+        __syncthreads();
         uint32_t *xk = a.skeys + (a.over_tuple_off[o] - a.over_base);
         TV *xv = static_cast<TV *>(a.svals) + (a.over_tuple_off[o] - a.over_base);
-        for (int64_t q = start + tid; q < end; q += DT) {
-            const uint32_t loc = xk[q] & (uint32_t)(W - 1);
-            atomicAdd(&acc[loc], (double)xv[q]);
-            seen[loc] = 1;  // every writer stores the same value
+        int64_t run = 0;  // merged entries written so far (the row's output is compacted to its start)
+        for (int d = 0; d < 256; ++d) {
+            const int64_t start = offs[d], end = offs[d + 1];
+            if (start >= end) continue;
+            for (int64_t q = start + tid; q < end; q += DT) {
+                const uint32_t loc = xk[q] & (uint32_t)(W - 1);
+                atomicAdd(&acc[loc], (double)xv[q]);
+                seen[loc] = 1;  // every writer stores the same value
+            }
+            __syncthreads();
+            uint32_t c = 0;
+            for (int i = c0t; i < c1t; ++i) c += seen[i];
+            int64_t total;
+            // output positions never pass the segment's own end: run + total <= end
+            int64_t pos = run + block_exclusive_scan<int64_t, DT>((int64_t)c, scratch, &total);
+            const uint32_t base = (uint32_t)d << w;
+            for (int i = c0t; i < c1t; ++i) {
+                if (!seen[i]) continue;
+                xk[pos] = base | (uint32_t)i;
+                xv[pos] = (TV)acc[i];
+                acc[i] = 0.0;
+                seen[i] = 0;
+                ++pos;
+            }
+            run += total;
+            __syncthreads();
         }
-        __syncthreads();
-        const int c0 = tid * per, c1 = min(c0 + per, W);
-        uint32_t c = 0;
-        for (int i = c0; i < c1; ++i) c += seen[i];
-        int64_t total;
-        int64_t pos = start + block_exclusive_scan<int64_t, DT>((int64_t)c, scratch, &total);
-        const uint32_t base = (uint32_t)d << w;
-        for (int i = c0; i < c1; ++i) {
-            if (!seen[i]) continue;
-            xk[pos] = base | (uint32_t)i;
-            xv[pos] = (TV)acc[i];
-            acc[i] = 0.0;
-            seen[i] = 0;
-            ++pos;
-        }
-        __syncthreads();
-        if (tid == 0) {
-            *slot = (int32_t)total;
-            if (total) atomicAdd(reinterpret_cast<unsigned long long *>(&a.over_u[o]), (unsigned long long)total);
-        }
-    }
-}
-
-// Per oversize row: the merged-entry counts of its 256 segments become their
-// exclusive prefixes (the segments' offsets inside the row's part of C).
-__global__ void __launch_bounds__(256) k_over_segscan(const OversizeArgs a) {
-    __shared__ int64_t scratch[40];
-    for (int64_t o = a.o_lo + blockIdx.x; o < a.o_hi; o += gridDim.x) {
-        int32_t *cnt = a.seg_cnt + (o - a.o_lo) * 256;
-        const int64_t v = cnt[threadIdx.x];
-        int64_t total;
-        const int64_t pre = block_exclusive_scan<int64_t, 256>(v, scratch, &total);
-        cnt[threadIdx.x] = (int32_t)pre;
-        __syncthreads();
+        if (tid == 0) a.over_u[o] = run;
     }
 }
 
 template <class TV>
 cudaError_t run_dense(const OversizeArgs &a, int num_sms, cudaStream_t s) {
     const int W = 1 << a.dense_shift;
-    const size_t smem = 8 * (size_t)W + (size_t)((W + 15) & ~15) + 8 * 40;
+    const size_t smem = 8 * (size_t)W + 8 * (264 + 40) + (size_t)((W + 15) & ~15);
     auto kern = k_over_dense<TV>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -278,40 +257,28 @@ cudaError_t run_dense(const OversizeArgs &a, int num_sms, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
     int64_t grid = (int64_t)num_sms * per_sm;
-    const int64_t items = (a.o_hi - a.o_lo) * 256;
-    if (grid > items) grid = items;
+    const int64_t rows = a.o_hi - a.o_lo;
+    if (grid > rows) grid = rows;
     if (grid < 1) return cudaSuccess;
     kern<<<(unsigned)grid, DT, smem, s>>>(a);
-    const int64_t no = a.o_hi - a.o_lo;
-    k_over_segscan<<<(unsigned)(no < (int64_t)num_sms * 8 ? no : (int64_t)num_sms * 8), 256, 0, s>>>(a);
-    count_launches(2);
+    count_launches(1);
     return cudaGetLastError();
 }
 
-// Copy each segment's merged entries to C at the row offset (recorded by the
-// sort kernel) plus the segment's offset inside the row; one warp per segment.
+// Copy each oversize row's merged entries (compacted to the start of its
+// scratch region) to C at the offset the sort kernel recorded; CTA per row.
 template <class TV, class OV>
 __global__ void __launch_bounds__(256) k_over_emit(const OversizeArgs a) {
-    const int lane = threadIdx.x & 31;
-    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     OV *valC = static_cast<OV *>(a.valC);
-    const int64_t nitems = (a.o_hi - a.o_lo) * 256;
-    for (int64_t item = warp; item < nitems; item += nwarps) {
-        const int64_t o = a.o_lo + item / 256;
-        const int d = (int)(item % 256);
+    for (int64_t o = a.o_lo + blockIdx.x; o < a.o_hi; o += gridDim.x) {
         const int64_t P = a.over_p[o];
         if (P < 0) continue;
-        const int32_t *off = a.seg_cnt + (o - a.o_lo) * 256;
-        const int64_t lo = off[d], hi = d < 255 ? (int64_t)off[d + 1] : a.over_u[o];
-        if (hi <= lo) continue;
-        int64_t start, end;
-        segment_range(a, o, d, &start, &end);
-        const uint32_t *xk = a.skeys + (a.over_tuple_off[o] - a.over_base) + start;
-        const TV *xv = static_cast<const TV *>(a.svals) + (a.over_tuple_off[o] - a.over_base) + start;
-        for (int64_t i = lane; i < hi - lo; i += 32) {
-            a.colidxC[P + lo + i] = (int32_t)xk[i];
-            valC[P + lo + i] = (OV)xv[i];
+        const int64_t U = a.over_u[o];
+        const uint32_t *xk = a.skeys + (a.over_tuple_off[o] - a.over_base);
+        const TV *xv = static_cast<const TV *>(a.svals) + (a.over_tuple_off[o] - a.over_base);
+        for (int64_t i = threadIdx.x; i < U; i += blockDim.x) {
+            a.colidxC[P + i] = (int32_t)xk[i];
+            valC[P + i] = (OV)xv[i];
         }
     }
 }
@@ -352,9 +319,9 @@ cudaError_t launch_oversize(const OversizeArgs &a, int passes, int dtype, int nu
 
 cudaError_t launch_oversize_emit(const OversizeArgs &a, int dtype, int num_sms, cudaStream_t s) {
     if (a.o_hi <= a.o_lo || !a.dense) return cudaSuccess;
-    const int64_t items = (a.o_hi - a.o_lo) * 256;
+    const int64_t rows = a.o_hi - a.o_lo;
     int64_t grid = (int64_t)num_sms * 8;
-    if (grid > ceil_div<int64_t>(items, 8)) grid = ceil_div<int64_t>(items, 8);
+    if (grid > rows) grid = rows;
     switch (dtype) {
         case PB_F64: k_over_emit<double, double><<<(unsigned)grid, 256, 0, s>>>(a); break;
         case PB_F32: k_over_emit<float, float><<<(unsigned)grid, 256, 0, s>>>(a); break;
