@@ -92,8 +92,21 @@ __global__ void __launch_bounds__(256) k_over_offsets(const OversizeArgs a) {
 }
 
 template <class TV>
+struct ScatterSmem {
+    uint32_t wc[256 * ONW];   // per (digit, warp) counts, then offsets inside the digit's run
+    uint32_t cbase[256];      // first position of each digit in the chunk's staged order
+    int64_t gbase[256];       // destination of a staged position i with digit d: gbase[d] + i
+    uint32_t sk[OVER_CHUNK];  // the chunk, staged in digit order
+    TV sv[OVER_CHUNK];
+};
+
+// Stable scatter of one chunk: ranks inside the chunk (warp multisplit), the
+// chunk staged in shared memory in digit order, then written out so that
+// consecutive threads write consecutive slots of each digit's run.
+template <class TV>
 __global__ void __launch_bounds__(OT) k_over_scatter(const OversizeArgs a, int pass, int shift) {
-    __shared__ uint32_t wc[256 * ONW];  // per (digit, warp) counts, then in-chunk offsets
+    extern __shared__ __align__(16) unsigned char smraw[];
+    ScatterSmem<TV> &m = *reinterpret_cast<ScatterSmem<TV> *>(smraw);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int64_t c = a.c_lo + blockIdx.x; c < a.c_hi; c += gridDim.x) {
         const ChunkRef r = chunk_ref(a, c);
@@ -102,7 +115,7 @@ __global__ void __launch_bounds__(OT) k_over_scatter(const OversizeArgs a, int p
         uint32_t *dk;
         TV *dv;
         pass_buffers<TV>(a, pass, r, sk, sv, dk, dv);
-        for (int i = threadIdx.x; i < 256 * ONW; i += OT) wc[i] = 0;
+        for (int i = threadIdx.x; i < 256 * ONW; i += OT) m.wc[i] = 0;
         __syncthreads();
         uint32_t kk[OE], lr[OE];
         TV vv[OE];
@@ -123,8 +136,8 @@ __global__ void __launch_bounds__(OT) k_over_scatter(const OversizeArgs a, int p
             const int leader = valid ? (__ffs(peers) - 1) : lane;
             uint32_t old = 0;
             if (valid && lane == leader) {
-                old = wc[dg * ONW + warp];
-                wc[dg * ONW + warp] = old + __popc(peers);
+                old = m.wc[dg * ONW + warp];
+                m.wc[dg * ONW + warp] = old + __popc(peers);
             }
             old = __shfl_sync(FULL, old, leader);
             __syncwarp();
@@ -132,13 +145,31 @@ __global__ void __launch_bounds__(OT) k_over_scatter(const OversizeArgs a, int p
             kk[j] = key;
         }
         __syncthreads();
-        // per digit: exclusive prefix over warps (stable order inside the chunk)
+        // per digit: exclusive prefix over warps (stable order inside the chunk), digit total
         if (threadIdx.x < 256) {
             uint32_t run = 0;
             for (int w = 0; w < ONW; ++w) {
-                const uint32_t v = wc[threadIdx.x * ONW + w];
-                wc[threadIdx.x * ONW + w] = run;
+                const uint32_t v = m.wc[threadIdx.x * ONW + w];
+                m.wc[threadIdx.x * ONW + w] = run;
                 run += v;
+            }
+            m.cbase[threadIdx.x] = run;
+        }
+        __syncthreads();
+        if (warp == 0) {  // exclusive scan of the digit totals: 8 digits per lane
+            uint32_t t[8], sum = 0;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                t[j] = m.cbase[lane * 8 + j];
+                sum += t[j];
+            }
+            uint32_t pre = warp_inclusive_scan(sum) - sum;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int d = lane * 8 + j;
+                m.cbase[d] = pre;
+                m.gbase[d] = (int64_t)a.hist[(c - a.c_lo) * 256 + d] - pre;
+                pre += t[j];
             }
         }
         __syncthreads();
@@ -147,10 +178,17 @@ __global__ void __launch_bounds__(OT) k_over_scatter(const OversizeArgs a, int p
             const int64_t q = warp * OWS + j * 32 + lane;
             if (q < r.len) {
                 const uint32_t dg = (kk[j] >> shift) & 255u;
-                const int64_t pos = (int64_t)a.hist[(c - a.c_lo) * 256 + dg] + wc[dg * ONW + warp] + lr[j];
-                dk[pos] = kk[j];
-                dv[pos] = vv[j];
+                const uint32_t local = m.cbase[dg] + m.wc[dg * ONW + warp] + lr[j];
+                m.sk[local] = kk[j];
+                m.sv[local] = vv[j];
             }
+        }
+        __syncthreads();
+        for (int64_t i = threadIdx.x; i < r.len; i += OT) {
+            const uint32_t key = m.sk[i];
+            const int64_t g = m.gbase[(key >> shift) & 255u] + i;
+            dk[g] = key;
+            dv[g] = m.sv[i];
         }
         __syncthreads();
     }
@@ -290,18 +328,21 @@ cudaError_t run_oversize(const OversizeArgs &a, int passes, int num_sms, cudaStr
     const unsigned ogrid = (unsigned)(no < g8 ? no : g8);
     cudaError_t e = cudaMemsetAsync(a.over_u + a.o_lo, 0, 8 * (size_t)no, s);
     if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_over_scatter<TV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sizeof(ScatterSmem<TV>));
+    if (e != cudaSuccess) return e;
     if (a.dense) {
         // one partition pass on the top digit, then dense accumulation per segment
         k_over_hist<TV><<<grid, OT, 0, s>>>(a, 0, a.dense_shift);
         k_over_offsets<<<ogrid, 256, 0, s>>>(a);
-        k_over_scatter<TV><<<grid, OT, 0, s>>>(a, 0, a.dense_shift);
+        k_over_scatter<TV><<<grid, OT, sizeof(ScatterSmem<TV>), s>>>(a, 0, a.dense_shift);
         count_launches(3);
         return run_dense<TV>(a, num_sms, s);
     }
     for (int pass = 0; pass < passes; ++pass) {
         k_over_hist<TV><<<grid, OT, 0, s>>>(a, pass, 8 * pass);
         k_over_offsets<<<ogrid, 256, 0, s>>>(a);
-        k_over_scatter<TV><<<grid, OT, 0, s>>>(a, pass, 8 * pass);
+        k_over_scatter<TV><<<grid, OT, sizeof(ScatterSmem<TV>), s>>>(a, pass, 8 * pass);
         count_launches(3);
     }
     k_over_heads<<<grid, OT, 0, s>>>(a, passes);
