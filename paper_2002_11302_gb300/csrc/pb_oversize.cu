@@ -104,7 +104,7 @@ struct ScatterSmem {
 // chunk staged in shared memory in digit order, then written out so that
 // consecutive threads write consecutive slots of each digit's run.
 template <class TV>
-__global__ void __launch_bounds__(OT) k_over_scatter(const OversizeArgs a, int pass, int shift) {
+__global__ void __launch_bounds__(OT, 2) k_over_scatter(const OversizeArgs a, int pass, int shift) {
     extern __shared__ __align__(16) unsigned char smraw[];
     ScatterSmem<TV> &m = *reinterpret_cast<ScatterSmem<TV> *>(smraw);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -228,10 +228,10 @@ __global__ void __launch_bounds__(OT) k_over_heads(const OversizeArgs a, int pas
 constexpr int DT = 256;  // threads per CTA of the dense kernels
 
 template <class TV>
-__global__ void __launch_bounds__(DT) k_over_dense(const OversizeArgs a) {
+__global__ void __launch_bounds__(DT) k_over_dense(const OversizeArgs a, int group) {
     extern __shared__ __align__(16) unsigned char sraw[];
     const int w = a.dense_shift;
-    const int W = 1 << w;
+    const int W = group << w;  // a round covers `group` consecutive digits
     double *acc = reinterpret_cast<double *>(sraw);
     int64_t *offs = reinterpret_cast<int64_t *>(acc + W);           // [257] segment starts of the row
     int64_t *scratch = offs + 264;
@@ -253,11 +253,12 @@ __global__ void __launch_bounds__(DT) k_over_dense(const OversizeArgs a) {
         uint32_t *xk = a.skeys + (a.over_tuple_off[o] - a.over_base);
         TV *xv = static_cast<TV *>(a.svals) + (a.over_tuple_off[o] - a.over_base);
         int64_t run = 0;  // merged entries written so far (the row's output is compacted to its start)
-        for (int d = 0; d < 256; ++d) {
-            const int64_t start = offs[d], end = offs[d + 1];
+        for (int d = 0; d < 256; d += group) {
+            const int64_t start = offs[d], end = offs[min(d + group, 256)];
             if (start >= end) continue;
+            const uint32_t base = (uint32_t)d << w;
             for (int64_t q = start + tid; q < end; q += DT) {
-                const uint32_t loc = xk[q] & (uint32_t)(W - 1);
+                const uint32_t loc = xk[q] - base;
                 atomicAdd(&acc[loc], (double)xv[q]);
                 seen[loc] = 1;  // every writer stores the same value
             }
@@ -265,12 +266,11 @@ __global__ void __launch_bounds__(DT) k_over_dense(const OversizeArgs a) {
             uint32_t c = 0;
             for (int i = c0t; i < c1t; ++i) c += seen[i];
             int64_t total;
-            // output positions never pass the segment's own end: run + total <= end
+            // output positions never pass the round's own end: run + total <= end
             int64_t pos = run + block_exclusive_scan<int64_t, DT>((int64_t)c, scratch, &total);
-            const uint32_t base = (uint32_t)d << w;
             for (int i = c0t; i < c1t; ++i) {
                 if (!seen[i]) continue;
-                xk[pos] = base | (uint32_t)i;
+                xk[pos] = base + (uint32_t)i;
                 xv[pos] = (TV)acc[i];
                 acc[i] = 0.0;
                 seen[i] = 0;
@@ -283,9 +283,15 @@ __global__ void __launch_bounds__(DT) k_over_dense(const OversizeArgs a) {
     }
 }
 
+// Columns of one dense round: consecutive digits grouped up to this width.
+constexpr int DENSE_ROUND_COLUMNS = 4096;
+
 template <class TV>
 cudaError_t run_dense(const OversizeArgs &a, int num_sms, cudaStream_t s) {
-    const int W = 1 << a.dense_shift;
+    int group = DENSE_ROUND_COLUMNS >> a.dense_shift;
+    if (group < 1) group = 1;
+    if (group > 256) group = 256;
+    const int W = group << a.dense_shift;
     const size_t smem = 8 * (size_t)W + 8 * (264 + 40) + (size_t)((W + 15) & ~15);
     auto kern = k_over_dense<TV>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -298,7 +304,7 @@ cudaError_t run_dense(const OversizeArgs &a, int num_sms, cudaStream_t s) {
     const int64_t rows = a.o_hi - a.o_lo;
     if (grid > rows) grid = rows;
     if (grid < 1) return cudaSuccess;
-    kern<<<(unsigned)grid, DT, smem, s>>>(a);
+    kern<<<(unsigned)grid, DT, smem, s>>>(a, group);
     count_launches(1);
     return cudaGetLastError();
 }
