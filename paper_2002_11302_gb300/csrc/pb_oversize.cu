@@ -280,6 +280,9 @@ __global__ void __launch_bounds__(DT) k_over_dense(const OversizeArgs a, int gro
             __syncthreads();
         }
         if (tid == 0) a.over_u[o] = run;
+        // every thread has read this row's offsets (trailing empty rounds included)
+        // before the next row's are stored
+        __syncthreads();
     }
 }
 
