@@ -319,11 +319,9 @@ pb_status pb_spgemm_symbolic(pb_handle *h, const pb_csc *A, const pb_csr *B, pb_
     // Oversize bins: work-item map for their global-memory radix sort.
     if (p->hdr.n_oversize > 0) {
         p->over_passes = (p->colbits + 7) / 8;
-        // Dense column tiles when the tuple and output value types agree (the merged
-        // sums are stored in the tuple slots) and order of sums need not be fixed.
+        // Dense column tiles when the order of the sums need not be fixed.
         const int shift = p->colbits > 8 ? p->colbits - 8 : 0;
-        p->over_dense = (dtype != PB_F64_F32TUPLE && !(cfg && cfg->deterministic) &&
-                         shift <= OVER_DENSE_MAX_SHIFT) ? 1 : 0;
+        p->over_dense = (!(cfg && cfg->deterministic) && shift <= OVER_DENSE_MAX_SHIFT) ? 1 : 0;
         p->over_shift = shift;
         if (p->over_dense) p->over_passes = 1;  // the one partition pass leaves the tuples in scratch
         p->over_map_bytes = align256(4 * (size_t)p->hdr.over_chunks);
@@ -573,6 +571,7 @@ static OversizeArgs oversize_args(const pb_plan *p, void *workspace, const pb_pa
     o.over_u = reinterpret_cast<int64_t *>(w + p->ws_over_u);
     o.dense = p->over_dense;
     o.dense_shift = p->over_shift;
+    o.wide = p->dtype == PB_F64_F32TUPLE ? 1 : 0;
     o.over_p = reinterpret_cast<int64_t *>(w + p->ws_overp);
     return o;
 }

@@ -97,6 +97,11 @@ struct OversizeArgs {
     // each tile of 2^dense_shift columns in shared memory
     int dense;
     int dense_shift;
+    // FP32 tuples merged into FP64 values (PB_F64_F32TUPLE): the dense kernel
+    // writes a row's merged values to the row's region of the main tuple buffer,
+    // free after the partition pass, as FP64 positions [0, h) over its key array
+    // and [h, U) over its value array, h = (N + 1) / 2 (N tuples, U merged)
+    int wide;
     int64_t *over_p;    // [n_over] C offset of each oversize row (-1: not written)
     int32_t *colidxC;   // C, for the copy of the segments once the offsets are known
     void *valC;

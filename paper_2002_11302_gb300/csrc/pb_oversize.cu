@@ -222,8 +222,10 @@ __global__ void __launch_bounds__(OT) k_over_heads(const OversizeArgs a, int pas
 // is kept, exact-zero sums included) and writes the merged entries back in
 // column order right after those of the previous segments.  The row's merged,
 // sorted entries (Sec. III-E) thus end up contiguous at the start of its
-// scratch region without a sort.  The order of the sums within a column is not
-// fixed (shared-memory atomics), so deterministic mode keeps the radix sort.
+// scratch region without a sort (with FP32 tuples the FP64 sums go to the row's
+// free region of the main tuple buffer instead; see OversizeArgs::wide).  The
+// order of the sums within a column is not fixed (shared-memory atomics), so
+// deterministic mode keeps the radix sort.
 // ---------------------------------------------------------------------------
 constexpr int DT = 256;  // threads per CTA of the dense kernels
 
@@ -252,6 +254,10 @@ __global__ void __launch_bounds__(DT) k_over_dense(const OversizeArgs a, int gro
         __syncthreads();
         uint32_t *xk = a.skeys + (a.over_tuple_off[o] - a.over_base);
         TV *xv = static_cast<TV *>(a.svals) + (a.over_tuple_off[o] - a.over_base);
+        // FP64 merged values of FP32 tuples: the row's main-buffer region (see OversizeArgs::wide)
+        const int64_t half = (N + 1) / 2;
+        double *wa = reinterpret_cast<double *>(a.keys + (a.bin_off[bin] - a.tuple_base));
+        double *wb = reinterpret_cast<double *>(static_cast<TV *>(a.vals) + (a.bin_off[bin] - a.tuple_base));
         int64_t run = 0;  // merged entries written so far (the row's output is compacted to its start)
         for (int d = 0; d < 256; d += group) {
             const int64_t start = offs[d], end = offs[min(d + group, 256)];
@@ -271,7 +277,10 @@ __global__ void __launch_bounds__(DT) k_over_dense(const OversizeArgs a, int gro
             for (int i = c0t; i < c1t; ++i) {
                 if (!seen[i]) continue;
                 xk[pos] = base + (uint32_t)i;
-                xv[pos] = (TV)acc[i];
+                if (a.wide)
+                    *(pos < half ? wa + pos : wb + (pos - half)) = acc[i];
+                else
+                    xv[pos] = (TV)acc[i];
                 acc[i] = 0.0;
                 seen[i] = 0;
                 ++pos;
@@ -314,7 +323,7 @@ cudaError_t run_dense(const OversizeArgs &a, int num_sms, cudaStream_t s) {
 
 // Copy each oversize row's merged entries (compacted to the start of its
 // scratch region) to C at the offset the sort kernel recorded; CTA per row.
-template <class TV, class OV>
+template <class TV, class OV, bool WIDE>
 __global__ void __launch_bounds__(256) k_over_emit(const OversizeArgs a) {
     OV *valC = static_cast<OV *>(a.valC);
     for (int64_t o = a.o_lo + blockIdx.x; o < a.o_hi; o += gridDim.x) {
@@ -322,10 +331,22 @@ __global__ void __launch_bounds__(256) k_over_emit(const OversizeArgs a) {
         if (P < 0) continue;
         const int64_t U = a.over_u[o];
         const uint32_t *xk = a.skeys + (a.over_tuple_off[o] - a.over_base);
-        const TV *xv = static_cast<const TV *>(a.svals) + (a.over_tuple_off[o] - a.over_base);
-        for (int64_t i = threadIdx.x; i < U; i += blockDim.x) {
-            a.colidxC[P + i] = (int32_t)xk[i];
-            valC[P + i] = (OV)xv[i];
+        if (WIDE) {
+            const int64_t bin = a.over_bin[o];
+            const int64_t half = (a.R[a.bin_row[bin + 1]] - a.R[a.bin_row[bin]] + 1) / 2;
+            const double *wa = reinterpret_cast<const double *>(a.keys + (a.bin_off[bin] - a.tuple_base));
+            const double *wb =
+                reinterpret_cast<const double *>(static_cast<const TV *>(a.vals) + (a.bin_off[bin] - a.tuple_base));
+            for (int64_t i = threadIdx.x; i < U; i += blockDim.x) {
+                a.colidxC[P + i] = (int32_t)xk[i];
+                valC[P + i] = (OV)(i < half ? wa[i] : wb[i - half]);
+            }
+        } else {
+            const TV *xv = static_cast<const TV *>(a.svals) + (a.over_tuple_off[o] - a.over_base);
+            for (int64_t i = threadIdx.x; i < U; i += blockDim.x) {
+                a.colidxC[P + i] = (int32_t)xk[i];
+                valC[P + i] = (OV)xv[i];
+            }
         }
     }
 }
@@ -373,9 +394,10 @@ cudaError_t launch_oversize_emit(const OversizeArgs &a, int dtype, int num_sms, 
     int64_t grid = (int64_t)num_sms * 8;
     if (grid > rows) grid = rows;
     switch (dtype) {
-        case PB_F64: k_over_emit<double, double><<<(unsigned)grid, 256, 0, s>>>(a); break;
-        case PB_F32: k_over_emit<float, float><<<(unsigned)grid, 256, 0, s>>>(a); break;
-        default: return cudaErrorInvalidValue;  // dense mode needs tuple and output types alike
+        case PB_F64: k_over_emit<double, double, false><<<(unsigned)grid, 256, 0, s>>>(a); break;
+        case PB_F32: k_over_emit<float, float, false><<<(unsigned)grid, 256, 0, s>>>(a); break;
+        case PB_F64_F32TUPLE: k_over_emit<float, double, true><<<(unsigned)grid, 256, 0, s>>>(a); break;
+        default: return cudaErrorInvalidValue;
     }
     count_launches(1);
     return cudaGetLastError();

@@ -88,6 +88,45 @@ def test_oversize_rows_counting_run_then_exact_c(pb):
     assert_matches(C, oracle.spgemm(A, B), EPS["f64"])
 
 
+def _revalue(A, B, av, bv):
+    return (synth.CSC(A.nrows, A.ncols, A.colptr, A.rowidx, av),
+            synth.CSR(B.nrows, B.ncols, B.rowptr, B.colidx, bv))
+
+
+def test_oversize_rows_integer_values_bit_exact(pb):
+    """Small integer values: every partial sum is exact in FP64, so the oracle's
+    sequential sums and the dense tiles' atomic sums (any order) agree bit for bit,
+    exact cancellations included."""
+    A, B = synth.rmat(12, 8, seed=43)
+    rng = np.random.default_rng(43)
+    A, B = _revalue(A, B, rng.integers(-3, 4, A.nnz).astype(np.float64),
+                    rng.integers(-3, 4, B.nnz).astype(np.float64))
+    assert int(np.max(oracle.row_flop(A, B))) > 4096
+    ref = oracle.spgemm(A, B)
+    assert np.any(ref.val == 0) and np.any(ref.absval[ref.val == 0] > 0), "no exact cancellation to check"
+    assert_matches(run(pb, A, B), ref, 0.0)
+
+
+@pytest.mark.parametrize("kind", ["wide", "subnormal", "huge"])
+def test_oversize_rows_outside_exact_window(pb, kind):
+    """Hub rows whose values span many binades, hold subnormals, or come near the
+    overflow range stay within the bound."""
+    A, B = synth.rmat(12, 8, seed=44)
+    rng = np.random.default_rng(44)
+    av, bv = A.val.copy(), B.val.copy()
+    if kind == "wide":
+        av[rng.random(A.nnz) < 0.1] *= 2.0 ** -80
+    elif kind == "subnormal":
+        pick = rng.random(B.nnz) < 0.02
+        bv[pick] = 5e-324 * rng.integers(1, 1000, int(pick.sum()))
+    else:
+        av *= 1e150
+        bv *= 1e150
+    A, B = _revalue(A, B, av, bv)
+    assert int(np.max(oracle.row_flop(A, B))) > 4096
+    assert_matches(run(pb, A, B), oracle.spgemm(A, B), EPS["f64"])
+
+
 def test_identity_and_permutation_bit_exact(pb):
     A, B = synth.er(5000, 6, seed=3)
     Ic, Ir = synth.identity(5000)
@@ -132,6 +171,42 @@ def test_fp32_tuples_fp64_merge(pb):
     assert C.val.dtype == torch.float64
     ref = oracle.spgemm(A, B)
     assert_matches(C, ref, EPS["f32"])
+
+
+@pytest.mark.parametrize("panels", [False, True])
+def test_fp32_tuples_oversize_rows_merge_in_fp64(pb, panels):
+    """FP32 tuples on hub rows above the bin capacity (dense tiles; the FP64 sums are kept
+    in the row's region of the main tuple buffer): structure exact, and every value of the
+    heaviest rows is the sum of the FP32-rounded products within the FP64 bound of that
+    sum, so the merge itself runs in FP64."""
+    import scipy.sparse as sp
+    A, B = synth.rmat(12, 8, seed=46)
+    rf = oracle.row_flop(A, B)
+    assert np.any((rf > 4096) & (rf % 2 == 1)), "want hub rows with an odd tuple count"
+    Ad, Bd = pb.csc_to_device(A), pb.csr_to_device(B)
+    cfg = pb.make_config(max_tuple_bytes=300000 * 8) if panels else None
+    plan = pb.symbolic(Ad, Bd, dtype=pb.PB_F64_F32TUPLE, config=cfg)
+    assert (plan.npanels > 1) == panels
+    C = pb.alloc_output(plan)
+    pb.numeric(plan, Ad, Bd, C, plan.workspace())
+    assert plan.status() == 0
+    n = int(C.rowptr[-1].item())
+    C = pb.CsrMatrix(C.nrows, C.ncols, C.rowptr, C.colidx[:n], C.val[:n])
+    assert C.val.dtype == torch.float64
+    assert_matches(C, oracle.spgemm(A, B), EPS["f32"])
+    rowptr, colidx, val = C.rowptr.cpu().numpy(), C.colidx.cpu().numpy(), C.val.cpu().numpy()
+    Ar = sp.csc_matrix((A.val, A.rowidx, A.colptr), shape=(A.nrows, A.ncols)).tocsr()
+    for i in np.argsort(rf)[-6:]:
+        ks, av = Ar.indices[Ar.indptr[i]:Ar.indptr[i + 1]], Ar.data[Ar.indptr[i]:Ar.indptr[i + 1]]
+        cols = np.concatenate([B.colidx[B.rowptr[k]:B.rowptr[k + 1]] for k in ks])
+        p32 = np.concatenate([(a * B.val[B.rowptr[k]:B.rowptr[k + 1]]).astype(np.float32) for k, a in zip(ks, av)])
+        p32 = p32.astype(np.float64)
+        want = np.bincount(cols, weights=p32, minlength=B.ncols)
+        mag = np.bincount(cols, weights=np.abs(p32), minlength=B.ncols)
+        a, b = rowptr[i], rowptr[i + 1]
+        assert np.array_equal(colidx[a:b], np.unique(cols))
+        err = np.abs(val[a:b] - want[colidx[a:b]])
+        assert np.all(err <= 64 * EPS["f64"] * mag[colidx[a:b]]), f"row {i}: merge not within the FP64 bound"
 
 
 def test_int32_rowptr_output(pb):
