@@ -51,11 +51,11 @@ WORKLOADS = {
                  desc="ER C=A*A, n=2^19, d=8 per column, FP64 values U(-1,1), int32 indices"),
     "er12": dict(kind="er", n=4096, d=4, seed=0, dtype="f64",
                  desc="ER C=A*A, n=4096, d=4 per column, FP64 values U(-1,1), int32 indices"),
-    "serve": dict(kind="serve", grids=(32, 64, 96, 128), scales=(14, 15, 16, 17, 18), ef=16, seed=6,
+    "serve": dict(kind="serve", grids=(32, 64, 96, 128), scales=(14, 15, 16, 17, 18, 19, 20), ef=16, seed=6,
                   budget=160 << 30, slots=4,
                   desc="Poisson-arrival request stream: AMG Galerkin P^T(A P) for the 3-D 7-point Poisson "
                        "matrix on 32^3..128^3 grids with 2x2x2 aggregation (FP64) mixed 1:1 with Markov-clustering "
-                       "squarings M*M of column-stochastic R-MAT matrices, scales 14..18, edge factor 16 (FP32); "
+                       "squarings M*M of column-stochastic R-MAT matrices, scales 14..20, edge factor 16 (FP32); "
                        "160 GiB HBM budget, 4 slots, operands resident"),
     "batch1024": dict(kind="batch", count=1024, seed=3, dtype="f64",
                       desc="1024 independent ER products A_i*A_i, n_i log-uniform in [512, 65536], d_i uniform "
@@ -546,14 +546,25 @@ def run_ours_serve(args, w):
     dev = [(kind, name, binding.csc_to_device(A, val_dtype=tdt[d]), binding.csr_to_device(B, val_dtype=tdt[d]),
             dts[d]) for kind, name, A, B, d in pool]
     handle = binding.Handle()
+    # plain calls size their work like the server: row panels of at most half the budget,
+    # and C sized by a counting run when a flop-sized C would not fit the budget
+    cfg = binding.make_config(max_tuple_bytes=w["budget"] // 2)
+    exact = []
+    for kind, _, Ad, Bd, dt in dev:
+        p = binding.symbolic(Ad, Bd, dtype=dt, config=cfg, handle=handle)
+        vb = 8 if dt == binding.PB_F64 else 4
+        exact.append(kind == "product" and p.workspace_bytes + p.flop * (4 + vb) + 8 * (Ad.nrows + 1) > w["budget"])
+        del p
 
     def plain(i):
         kind, _, Ad, Bd, dt = dev[i]
         if kind == "galerkin":
-            AP = binding.spgemm(Ad, Bd, dtype=dt, rowptr64=False, handle=handle)
+            AP = binding.spgemm(Ad, Bd, dtype=dt, config=cfg, rowptr64=False, handle=handle)
             PT = binding.CscMatrix(Bd.ncols, Bd.nrows, Bd.rowptr, Bd.colidx, Bd.val)
-            return binding.spgemm(PT, AP, dtype=dt, handle=handle)
-        return binding.spgemm(Ad, Bd, dtype=dt, handle=handle)
+            return binding.spgemm(PT, AP, dtype=dt, config=cfg, handle=handle)
+        if exact[i]:
+            return binding.spgemm_exact(Ad, Bd, dtype=dt, config=cfg, handle=handle)[0]
+        return binding.spgemm(Ad, Bd, dtype=dt, config=cfg, handle=handle)
 
     # flop of every request kind (both products of a Galerkin request) and its plain service time
     flops, service = [], []
