@@ -40,6 +40,10 @@ WORKLOADS = {
                  desc="ER C=A*A, n=2^21, d=8 per column, FP64 values U(-1,1), int32 indices"),
     "rmat20": dict(kind="rmat", scale=20, ef=16, seed=2, dtype="f64", budget=64 << 30, exact=True,
                    desc="R-MAT C=A*A, scale 20, edge factor 16, (0.57,0.19,0.19,0.05), dedup, FP64, row panels"),
+    "rmat18": dict(kind="rmat", scale=18, ef=16, seed=2, dtype="f64",
+                   desc="R-MAT C=A*A, scale 18, edge factor 16, (0.57,0.19,0.19,0.05), dedup, FP64"),
+    "rmat16": dict(kind="rmat", scale=16, ef=16, seed=2, dtype="f64",
+                   desc="R-MAT C=A*A, scale 16, edge factor 16, (0.57,0.19,0.19,0.05), dedup, FP64"),
     "rmat20f32t": dict(kind="rmat", scale=20, ef=16, seed=2, dtype="f64_f32tuple", budget=64 << 30, exact=True,
                        desc="R-MAT C=A*A, scale 20, edge factor 16, (0.57,0.19,0.19,0.05), dedup, FP64 values, "
                             "FP32 tuples merged in FP64, row panels"),
