@@ -93,8 +93,10 @@ typedef struct pb_csr_out { /* C: nrows x ncols in CSR; exactly one of rowptr64/
 
 /* Tunables.  Zero in any field selects the built-in default. */
 typedef struct pb_config {
-    int32_t bin_capacity;    /* max tuples of one bin sorted on-chip (power of two, 1024..16384) */
-    int32_t sort_threads;    /* threads of one sort CTA (256 or 512)                           */
+    int32_t bin_capacity;    /* max tuples of one bin sorted on-chip: 2048, 4096 (default) or 8192;
+                                other values give PB_ERR_INVALID_ARG                             */
+    int32_t sort_threads;    /* threads of one sort CTA: fixed at bin_capacity / 8 (256, 512, 1024);
+                                0 or that value, anything else gives PB_ERR_INVALID_ARG           */
     int32_t expand_chunk;    /* tuples per expand work item                                     */
     int32_t deterministic;   /* nonzero: bitwise-reproducible values.  The plan fixes every A entry's
                                 tuple positions (CSC order inside each bin) instead of atomic cursors,

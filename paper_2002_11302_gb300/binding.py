@@ -274,8 +274,9 @@ def default_handle() -> Handle:
 
 
 def make_config(bin_capacity: int = 0, expand_chunk: int = 0, max_tuple_bytes: int = 0,
-                deterministic: bool = False, min_panels: int = 0) -> _Config:
-    return _Config(bin_capacity, 0, expand_chunk, 1 if deterministic else 0, max_tuple_bytes, min_panels)
+                deterministic: bool = False, min_panels: int = 0, sort_threads: int = 0) -> _Config:
+    return _Config(bin_capacity, sort_threads, expand_chunk, 1 if deterministic else 0, max_tuple_bytes,
+                   min_panels)
 
 
 class Plan:

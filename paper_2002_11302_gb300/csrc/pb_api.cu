@@ -208,6 +208,10 @@ pb_status pb_spgemm_symbolic(pb_handle *h, const pb_csc *A, const pb_csr *B, pb_
         delete p;
         return fail(h, PB_ERR_INVALID_ARG, "bin_capacity must be 2048, 4096 or 8192");
     }
+    if (cfg && cfg->sort_threads && cfg->sort_threads != p->capacity / 8) {
+        delete p;
+        return fail(h, PB_ERR_INVALID_ARG, "sort_threads must be 0 or bin_capacity / 8");
+    }
     p->heavy = p->capacity / 2;
     if (cfg && cfg->expand_chunk) {
         if (cfg->expand_chunk < 32 || cfg->expand_chunk % 32) {

@@ -209,6 +209,20 @@ def test_fp32_tuples_oversize_rows_merge_in_fp64(pb, panels):
         assert np.all(err <= 64 * EPS["f64"] * mag[colidx[a:b]]), f"row {i}: merge not within the FP64 bound"
 
 
+def test_config_validation(pb):
+    """Unsupported tunables are refused by the symbolic phase, not ignored."""
+    A, B = synth.er(2000, 4, seed=13)
+    Ad, Bd = pb.csc_to_device(A), pb.csr_to_device(B)
+    for bad in (dict(bin_capacity=3000), dict(bin_capacity=1024), dict(sort_threads=256),
+                dict(bin_capacity=8192, sort_threads=512), dict(expand_chunk=100)):
+        with pytest.raises(pb.PBError) as e:
+            pb.symbolic(Ad, Bd, config=pb.make_config(**bad))
+        assert e.value.status == 1, bad  # PB_ERR_INVALID_ARG
+    for cap in (2048, 4096, 8192):
+        C = pb.spgemm(Ad, Bd, config=pb.make_config(bin_capacity=cap, sort_threads=cap // 8))
+        assert_matches(C, oracle.spgemm(A, B), EPS["f64"])
+
+
 def test_int32_rowptr_output(pb):
     A, B = synth.er(10000, 4, seed=12)
     C = run(pb, A, B, rowptr64=False)
