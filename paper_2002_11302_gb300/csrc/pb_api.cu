@@ -576,6 +576,7 @@ static OversizeArgs oversize_args(const pb_plan *p, void *workspace, const pb_pa
     o.dense = p->over_dense;
     o.dense_shift = p->over_shift;
     o.wide = p->dtype == PB_F64_F32TUPLE ? 1 : 0;
+    o.row_ticket = reinterpret_cast<uint32_t *>(w + p->ws_ctrl) + 16;  // word 0 is the sort's ticket
     o.over_p = reinterpret_cast<int64_t *>(w + p->ws_overp);
     return o;
 }

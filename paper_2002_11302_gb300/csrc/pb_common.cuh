@@ -102,6 +102,7 @@ struct OversizeArgs {
     // free after the partition pass, as FP64 positions [0, h) over its key array
     // and [h, U) over its value array, h = (N + 1) / 2 (N tuples, U merged)
     int wide;
+    uint32_t *row_ticket;  // [2] zeroed per panel: rows taken in order by the dense and emit kernels
     int64_t *over_p;    // [n_over] C offset of each oversize row (-1: not written)
     int32_t *colidxC;   // C, for the copy of the segments once the offsets are known
     void *valC;

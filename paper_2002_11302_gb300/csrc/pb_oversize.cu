@@ -245,7 +245,14 @@ __global__ void __launch_bounds__(DT) k_over_dense(const OversizeArgs a, int gro
     }
     const int per = (W + DT - 1) / DT;  // tile columns per thread in the compaction (contiguous)
     const int c0t = tid * per, c1t = min(c0t + per, W);
-    for (int64_t o = a.o_lo + blockIdx.x; o < a.o_hi; o += gridDim.x) {
+    __shared__ int64_t next_row;
+    while (true) {
+        // rows are taken in order through a ticket (hub rows come first), so the
+        // largest rows start early and the rest balance around them
+        if (tid == 0) next_row = a.o_lo + (int64_t)atomicAdd(&a.row_ticket[0], 1u);
+        __syncthreads();
+        const int64_t o = next_row;
+        if (o >= a.o_hi) break;
         const int64_t bin = a.over_bin[o];
         const int64_t N = a.R[a.bin_row[bin + 1]] - a.R[a.bin_row[bin]];
         const int64_t c0 = a.over_chunk_off[o] - a.c_lo;  // the bin's first work item holds its digit offsets
@@ -290,7 +297,7 @@ __global__ void __launch_bounds__(DT) k_over_dense(const OversizeArgs a, int gro
         }
         if (tid == 0) a.over_u[o] = run;
         // every thread has read this row's offsets (trailing empty rounds included)
-        // before the next row's are stored
+        // and its ticket before the next row's are stored
         __syncthreads();
     }
 }
@@ -326,7 +333,13 @@ cudaError_t run_dense(const OversizeArgs &a, int num_sms, cudaStream_t s) {
 template <class TV, class OV, bool WIDE>
 __global__ void __launch_bounds__(256) k_over_emit(const OversizeArgs a) {
     OV *valC = static_cast<OV *>(a.valC);
-    for (int64_t o = a.o_lo + blockIdx.x; o < a.o_hi; o += gridDim.x) {
+    __shared__ int64_t next_row;
+    while (true) {
+        if (threadIdx.x == 0) next_row = a.o_lo + (int64_t)atomicAdd(&a.row_ticket[1], 1u);
+        __syncthreads();
+        const int64_t o = next_row;
+        __syncthreads();  // every thread has its row before the ticket word is reused
+        if (o >= a.o_hi) break;
         const int64_t P = a.over_p[o];
         if (P < 0) continue;
         const int64_t U = a.over_u[o];

@@ -59,6 +59,16 @@ def test_host_product_rmat_oversize_rows_in_panels(pb):
     assert_matches(trimmed(C, nnz, B.ncols), oracle.spgemm(A, B), EPS["f64"])
 
 
+def test_host_product_rmat_fp32_tuples_in_panels(pb):
+    """FP32 tuples with hub rows (dense tiles keep their FP64 sums in the main tuple
+    buffer) and row panels copied back one by one."""
+    A, B = synth.rmat(13, 8, seed=32)
+    assert int(np.max(oracle.row_flop(A, B))) > 4096
+    C, nnz, st = run_host(pb, A, B, dtype=2, min_panels=3)
+    assert st == 0 and C.val.dtype == torch.float64
+    assert_matches(trimmed(C, nnz, B.ncols), oracle.spgemm(A, B), EPS["f32"])
+
+
 def test_host_product_fp32(pb):
     A, B = synth.er(20000, 6, seed=5)
     A32 = synth.CSC(A.nrows, A.ncols, A.colptr, A.rowidx, A.val.astype(np.float32))
