@@ -56,7 +56,7 @@ struct pb_plan {
     int over_dense = 0, over_shift = 0;  // oversize rows merged in dense column tiles
     // workspace layout of the numeric phase
     size_t ws_keys = 0, ws_vals = 0, ws_cursor = 0, ws_status = 0, ws_ctrl = 0;
-    size_t ws_skeys = 0, ws_svals = 0, ws_hist = 0, ws_over_u = 0, ws_overp = 0, ws_bytes = 0;
+    size_t ws_skeys = 0, ws_svals = 0, ws_hist = 0, ws_over_u = 0, ws_overp = 0, ws_overord = 0, ws_bytes = 0;
 };
 
 namespace {
@@ -479,6 +479,8 @@ pb_status pb_spgemm_symbolic(pb_handle *h, const pb_csc *A, const pb_csr *B, pb_
     w += align256(8 * NO);
     p->ws_overp = w;
     w += align256(8 * NO);
+    p->ws_overord = w;  // dense path: row order (int32 per row) and 128 class counters
+    w += p->over_dense ? align256(4 * NO) + 512 : 0;
     p->ws_bytes = w;
     *out = p;
     return PB_OK;
@@ -577,6 +579,8 @@ static OversizeArgs oversize_args(const pb_plan *p, void *workspace, const pb_pa
     o.dense_shift = p->over_shift;
     o.wide = p->dtype == PB_F64_F32TUPLE ? 1 : 0;
     o.row_ticket = reinterpret_cast<uint32_t *>(w + p->ws_ctrl) + 16;  // word 0 is the sort's ticket
+    o.row_order = reinterpret_cast<int32_t *>(w + p->ws_overord);
+    o.order_cnt = reinterpret_cast<uint32_t *>(w + p->ws_overord + align256(4 * (size_t)p->hdr.n_oversize));
     o.over_p = reinterpret_cast<int64_t *>(w + p->ws_overp);
     return o;
 }

@@ -103,6 +103,8 @@ struct OversizeArgs {
     // and [h, U) over its value array, h = (N + 1) / 2 (N tuples, U merged)
     int wide;
     uint32_t *row_ticket;  // [2] zeroed per panel: rows taken in order by the dense and emit kernels
+    int32_t *row_order;    // [o_hi - o_lo] the panel's rows (minus o_lo) by decreasing size class
+    uint32_t *order_cnt;   // [128] per size class: rows, then rows placed
     int64_t *over_p;    // [n_over] C offset of each oversize row (-1: not written)
     int32_t *colidxC;   // C, for the copy of the segments once the offsets are known
     void *valC;

@@ -213,6 +213,37 @@ __global__ void __launch_bounds__(OT) k_over_heads(const OversizeArgs a, int pas
 }
 
 
+// Rows of the panel by decreasing size class (leading zeros of the tuple count):
+// the dense and emit kernels take rows in this order through a ticket, so the
+// largest start first and the rest fill in around them (longest-first list
+// scheduling within a factor of two).
+__device__ inline int over_size_class(const OversizeArgs &a, int64_t o) {
+    const int64_t bin = a.over_bin[o];
+    const int64_t N = a.R[a.bin_row[bin + 1]] - a.R[a.bin_row[bin]];
+    return __clzll((long long)(N > 0 ? N : 1));
+}
+
+__global__ void k_over_order_count(const OversizeArgs a) {
+    for (int64_t o = a.o_lo + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < a.o_hi;
+         o += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(&a.order_cnt[over_size_class(a, o)], 1u);
+}
+
+__global__ void k_over_order_place(const OversizeArgs a) {
+    __shared__ uint32_t start[64];
+    if (threadIdx.x < 64) {
+        uint32_t s = 0;
+        for (int k = 0; k < (int)threadIdx.x; ++k) s += a.order_cnt[k];
+        start[threadIdx.x] = s;
+    }
+    __syncthreads();
+    for (int64_t o = a.o_lo + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < a.o_hi;
+         o += (int64_t)gridDim.x * blockDim.x) {
+        const int c = over_size_class(a, o);
+        a.row_order[start[c] + atomicAdd(&a.order_cnt[64 + c], 1u)] = (int32_t)(o - a.o_lo);
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Dense tiles for oversize rows.  After one partition pass on the column's top
 // digit (column >> dense_shift), the tuples of an oversize row with digit d form
@@ -247,9 +278,11 @@ __global__ void __launch_bounds__(DT) k_over_dense(const OversizeArgs a, int gro
     const int c0t = tid * per, c1t = min(c0t + per, W);
     __shared__ int64_t next_row;
     while (true) {
-        // rows are taken in order through a ticket (hub rows come first), so the
-        // largest rows start early and the rest balance around them
-        if (tid == 0) next_row = a.o_lo + (int64_t)atomicAdd(&a.row_ticket[0], 1u);
+        // rows are taken through a ticket, largest size class first
+        if (tid == 0) {
+            const int64_t t = (int64_t)atomicAdd(&a.row_ticket[0], 1u);
+            next_row = t < a.o_hi - a.o_lo ? a.o_lo + a.row_order[t] : a.o_hi;
+        }
         __syncthreads();
         const int64_t o = next_row;
         if (o >= a.o_hi) break;
@@ -335,7 +368,10 @@ __global__ void __launch_bounds__(256) k_over_emit(const OversizeArgs a) {
     OV *valC = static_cast<OV *>(a.valC);
     __shared__ int64_t next_row;
     while (true) {
-        if (threadIdx.x == 0) next_row = a.o_lo + (int64_t)atomicAdd(&a.row_ticket[1], 1u);
+        if (threadIdx.x == 0) {
+            const int64_t t = (int64_t)atomicAdd(&a.row_ticket[1], 1u);
+            next_row = t < a.o_hi - a.o_lo ? a.o_lo + a.row_order[t] : a.o_hi;
+        }
         __syncthreads();
         const int64_t o = next_row;
         __syncthreads();  // every thread has its row before the ticket word is reused
@@ -379,7 +415,10 @@ cudaError_t run_oversize(const OversizeArgs &a, int passes, int num_sms, cudaStr
         k_over_hist<TV><<<grid, OT, 0, s>>>(a, 0, a.dense_shift);
         k_over_offsets<<<ogrid, 256, 0, s>>>(a);
         k_over_scatter<TV><<<grid, OT, sizeof(ScatterSmem<TV>), s>>>(a, 0, a.dense_shift);
-        count_launches(3);
+        if ((e = cudaMemsetAsync(a.order_cnt, 0, 512, s)) != cudaSuccess) return e;
+        k_over_order_count<<<ogrid, 256, 0, s>>>(a);
+        k_over_order_place<<<ogrid, 256, 0, s>>>(a);
+        count_launches(5);
         return run_dense<TV>(a, num_sms, s);
     }
     for (int pass = 0; pass < passes; ++pass) {
