@@ -259,6 +259,8 @@ __global__ void k_over_order_place(const OversizeArgs a) {
 // deterministic mode keeps the radix sort.
 // ---------------------------------------------------------------------------
 constexpr int DT = 256;  // threads per CTA of the dense kernels
+// (slab, warp) counters of the compaction: up to 2^OVER_DENSE_MAX_SHIFT columns per round
+constexpr int DENSE_WCNT = ((1 << OVER_DENSE_MAX_SHIFT) / DT) * (DT / 32);
 
 template <class TV>
 __global__ void __launch_bounds__(DT) k_over_dense(const OversizeArgs a, int group) {
@@ -268,14 +270,16 @@ __global__ void __launch_bounds__(DT) k_over_dense(const OversizeArgs a, int gro
     double *acc = reinterpret_cast<double *>(sraw);
     int64_t *offs = reinterpret_cast<int64_t *>(acc + W);           // [257] segment starts of the row
     int64_t *scratch = offs + 264;
-    uint8_t *seen = reinterpret_cast<uint8_t *>(scratch + 40);       // presence of each column of the tile
-    const int tid = threadIdx.x;
+    uint32_t *wtot = reinterpret_cast<uint32_t *>(scratch);          // merged entries of the round
+    uint32_t *wcnt = reinterpret_cast<uint32_t *>(scratch + 40);     // [W / DT * NWD] per (slab, warp)
+    uint8_t *seen = reinterpret_cast<uint8_t *>(wcnt + DENSE_WCNT);  // presence of each column of the tile
+    constexpr int NWD = DT / 32;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     for (int i = tid; i < W; i += DT) {
         acc[i] = 0.0;
         seen[i] = 0;
     }
-    const int per = (W + DT - 1) / DT;  // tile columns per thread in the compaction (contiguous)
-    const int c0t = tid * per, c1t = min(c0t + per, W);
+    const int nslab = W / DT;  // W is a multiple of DT
     __shared__ int64_t next_row;
     while (true) {
         // rows are taken through a ticket, largest size class first
@@ -309,23 +313,46 @@ __global__ void __launch_bounds__(DT) k_over_dense(const OversizeArgs a, int gro
                 seen[loc] = 1;  // every writer stores the same value
             }
             __syncthreads();
-            uint32_t c = 0;
-            for (int i = c0t; i < c1t; ++i) c += seen[i];
-            int64_t total;
-            // output positions never pass the round's own end: run + total <= end
-            int64_t pos = run + block_exclusive_scan<int64_t, DT>((int64_t)c, scratch, &total);
-            for (int i = c0t; i < c1t; ++i) {
-                if (!seen[i]) continue;
-                xk[pos] = base + (uint32_t)i;
-                if (a.wide)
-                    *(pos < half ? wa + pos : wb + (pos - half)) = acc[i];
-                else
-                    xv[pos] = (TV)acc[i];
-                acc[i] = 0.0;
-                seen[i] = 0;
-                ++pos;
+            // Compaction in column order.  Warp v owns column sl*DT + v*32 + lane of
+            // each slab sl of DT columns: lanes touch consecutive flags and
+            // accumulators (no bank conflicts) and write consecutive output slots.
+            for (int sl = 0; sl < nslab; ++sl) {
+                const uint32_t m = __ballot_sync(FULL, seen[sl * DT + tid] != 0);
+                if (lane == 0) wcnt[sl * NWD + wid] = (uint32_t)__popc(m);
             }
-            run += total;
+            __syncthreads();
+            if (wid == 0) {  // exclusive scan of the (slab, warp) counts, i.e. in column order
+                const int n = nslab * NWD, k = (n + 31) / 32;
+                uint32_t sum = 0;
+                for (int j = 0; j < k; ++j) sum += (lane * k + j < n) ? wcnt[lane * k + j] : 0u;
+                uint32_t pre = warp_inclusive_scan(sum) - sum;
+                for (int j = 0; j < k; ++j) {
+                    if (lane * k + j < n) {
+                        const uint32_t v = wcnt[lane * k + j];
+                        wcnt[lane * k + j] = pre;
+                        pre += v;
+                    }
+                }
+                if (lane == 31) *wtot = pre;
+            }
+            __syncthreads();
+            // output positions never pass the round's own end: run + *wtot <= end
+            for (int sl = 0; sl < nslab; ++sl) {
+                const int i = sl * DT + tid;
+                const bool on = seen[i] != 0;
+                const uint32_t m = __ballot_sync(FULL, on);
+                if (on) {
+                    const int64_t pos = run + wcnt[sl * NWD + wid] + __popc(m & lanemask_lt());
+                    xk[pos] = base + (uint32_t)i;
+                    if (a.wide)
+                        *(pos < half ? wa + pos : wb + (pos - half)) = acc[i];
+                    else
+                        xv[pos] = (TV)acc[i];
+                    acc[i] = 0.0;
+                    seen[i] = 0;
+                }
+            }
+            run += *wtot;
             __syncthreads();
         }
         if (tid == 0) a.over_u[o] = run;
@@ -344,7 +371,7 @@ cudaError_t run_dense(const OversizeArgs &a, int num_sms, cudaStream_t s) {
     if (group < 1) group = 1;
     if (group > 256) group = 256;
     const int W = group << a.dense_shift;
-    const size_t smem = 8 * (size_t)W + 8 * (264 + 40) + (size_t)((W + 15) & ~15);
+    const size_t smem = 8 * (size_t)W + 8 * (264 + 40) + 4 * (size_t)DENSE_WCNT + (size_t)((W + 15) & ~15);
     auto kern = k_over_dense<TV>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
