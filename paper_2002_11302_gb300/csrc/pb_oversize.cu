@@ -2,17 +2,22 @@
 //
 // The paper keeps every bin sortable in cache by using more bins or variable
 // row ranges (Sec. III-D); a single row cannot be split by rows, so its tuples
-// (all with in-bin row 0, key = column) are sorted here by a segmented, stable
-// LSD radix sort in global memory, 8 bits per pass:
-//   histogram  per chunk of CHUNK tuples, counts of each digit value;
-//   offsets    per oversize bin, for every (digit, chunk) the destination of
+// (all with in-bin row 0, key = column) are merged here in global memory.
+// Both paths start from the same stable partition in chunks of OVER_CHUNK tuples:
+//   histogram  per chunk, counts of each 8-bit digit value;
+//   offsets    per oversize row, for every (digit, chunk) the destination of
 //              the chunk's first tuple with that digit (digit-major order);
 //   scatter    each chunk ranks its tuples stably (warp multisplit over the
-//              digit with ballots, per-warp counters) and writes them out.
-// Passes alternate between the bin's region of the tuple buffer and a scratch
-// region.  Afterwards a head count gives the number of merged entries of each
-// oversize bin, so the look-back chain of the sort phase never waits for the
-// merge itself; the sort kernel then streams the sorted run into C.
+//              digit with ballots, per-warp counters), stages them in shared
+//              memory in digit order and writes them out coalesced.
+// Dense path (default): one pass on the column's top 8 bits, then each row is
+// merged in dense shared-memory tiles in column order (k_over_dense) and later
+// copied into C at the offset the sort kernel found (k_over_emit).
+// Radix path (deterministic mode, or columns too wide for a tile): LSD passes
+// over all key bits alternate between the row's region of the tuple buffer and
+// a scratch region; a head count then gives each row's merged size, so the
+// look-back chain of the sort phase never waits for the merge itself, and the
+// sort kernel streams the sorted run into C.
 #include "pb_common.cuh"
 
 namespace pb {
