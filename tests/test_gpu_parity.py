@@ -93,6 +93,17 @@ def _revalue(A, B, av, bv):
             synth.CSR(B.nrows, B.ncols, B.rowptr, B.colidx, bv))
 
 
+@pytest.mark.parametrize("n", [1, 37, 256, 300, 1000])
+@pytest.mark.parametrize("dtype", [0, 2])
+def test_oversize_rows_narrow_b(pb, n, dtype):
+    """Hub rows when B has few columns: tiles narrower than 4096 columns (one or two
+    warp slabs of 256), and many duplicates per column; FP64 and FP32 tuples."""
+    A, _ = synth.random_sparse(5, 6000, 0.8, seed=50 + n)
+    _, B = synth.random_sparse(6000, n, min(1.0, 3.0 / n), seed=60 + n)
+    assert int(np.max(oracle.row_flop(A, B))) > 4096
+    assert_matches(run(pb, A, B, dtype=dtype), oracle.spgemm(A, B), EPS["f64"] if dtype == 0 else EPS["f32"])
+
+
 def test_oversize_rows_integer_values_bit_exact(pb):
     """Small integer values: every partial sum is exact in FP64, so the oracle's
     sequential sums and the dense tiles' atomic sums (any order) agree bit for bit,
