@@ -72,6 +72,21 @@ def test_dense_bruteforce(seed):
         assert np.all(np.diff(seg) > 0)
 
 
+def test_zero_values_keep_structure():
+    """No dropping (Sec. III-E merges equal keys without a value test): with every value
+    zero, C's structure is still the boolean product of the stored patterns, and every
+    value and magnitude sum is exactly zero."""
+    A, B = synth.rmat(7, 8, seed=3)
+    Az = synth.CSC(A.nrows, A.ncols, A.colptr, A.rowidx, np.zeros_like(A.val))
+    Bz = synth.CSR(B.nrows, B.ncols, B.rowptr, B.colidx, np.zeros_like(B.val))
+    C = oracle.spgemm(Az, Bz)
+    _, Cpat = to_dense(C, A.nrows, B.ncols)
+    ref_pat = (pattern_of(synth.csc_to_csr(Az)) @ pattern_of(Bz)) > 0
+    assert ref_pat.any()
+    assert np.array_equal(Cpat.astype(bool), ref_pat)
+    assert not np.any(C.val) and not np.any(C.absval)
+
+
 def test_rows_subset_matches_full():
     A, B = synth.er(300, 5, seed=7)
     full = oracle.spgemm(A, B)
