@@ -252,11 +252,14 @@ __global__ void k_over_order_place(const OversizeArgs a) {
 // ---------------------------------------------------------------------------
 // Dense tiles for oversize rows.  After one partition pass on the column's top
 // digit (column >> dense_shift), the tuples of an oversize row with digit d form
-// one contiguous segment of the scratch buffer.  One CTA per row walks its
-// segments in digit order; it sums each into a dense shared-memory tile of
-// 2^dense_shift FP64 accumulators with presence flags (every structural entry
-// is kept, exact-zero sums included) and writes the merged entries back in
-// column order right after those of the previous segments.  The row's merged,
+// one contiguous segment of the scratch buffer.  A CTA takes one row at a time
+// (through a ticket, largest size class first) and walks its segments in digit
+// order, a round of whole digits of up to 4096 columns at a time; it sums each
+// round into a dense shared-memory tile of FP64 accumulators with presence flags
+// (every structural entry is kept, exact-zero sums included) and writes the
+// merged entries back in column order right after those of the previous rounds.
+// The compaction goes by warp and slab (lanes on consecutive columns), so it
+// reads the tile without bank conflicts and writes coalesced.  The row's merged,
 // sorted entries (Sec. III-E) thus end up contiguous at the start of its
 // scratch region without a sort (with FP32 tuples the FP64 sums go to the row's
 // free region of the main tuple buffer instead; see OversizeArgs::wide).  The
