@@ -4,23 +4,22 @@
 //   load     the bin's keys and values with two bulk global->shared copies
 //            (the bin is read from DRAM exactly once: "in-cache sorting",
 //            Sec. III-D, with shared memory playing the cache);
-//   sort     by the packed (in-bin row, column) key (Sec. III-D).  A bucket
-//            pass on the top bits of (key - min key) with shared-memory atomic
-//            counters places every tuple in its bucket.  When no bucket holds
-//            more than SMALL_BUCKET tuples (the common case for ER-like
-//            inputs), each thread owns a contiguous run of buckets and
-//            finishes them by insertion sort.  Otherwise a stable LSD radix
-//            sort over 8-bit digits (warp-level multisplit ranking with
-//            ballots) sorts the whole bin.  Both give ascending keys; equal
-//            keys are merged next, so their relative order does not matter;
-//   compress equal adjacent keys are summed (Sec. III-E: one pass over the
-//            sorted tuples; sums accumulate in double);
+//   sort     by the packed (in-bin row, column) key (Sec. III-D): a bucket
+//            pass on the key's top bits with shared-memory atomic counters,
+//            then a rank inside the few multi-tuple buckets; a bin with a
+//            bucket above SMALL_BUCKET tuples is sorted by a stable LSD radix
+//            sort over 8-bit digits instead;
+//   compress equal adjacent keys are summed (Sec. III-E; sums accumulate in
+//            double);
 //   ConvertCSR the bins are concatenated in row order: the bin's number of
 //            merged entries is published and the exclusive prefix over all
-//            earlier bins is found by a warp-parallel decoupled look-back
-//            (bins are taken in increasing order through a ticket counter, so
-//            every bin a CTA waits for is owned by a running CTA); then the
-//            column indices, values and row pointers of the bin are written.
+//            earlier bins is found by a decoupled look-back (bins are taken in
+//            increasing order through a ticket counter, so every bin a CTA
+//            waits for is owned by a running CTA); then the column indices,
+//            values and row pointers of the bin are written.
+// Two kernels: k_binsort for single products (phases described above it) and
+// k_binsort_batch for batched products (bins of many products in one launch,
+// each bin writing into its own product's C).
 #include "pb_common.cuh"
 
 namespace pb {
@@ -64,7 +63,7 @@ struct SortSmem {
     uint32_t rowcnt[RMAX];  // merged entries per in-bin row
     int64_t scratch[40];
     uint32_t wtot[NW];      // merged entries per warp segment
-    int32_t marks[2];       // look-back: nearest inclusive prefix / unpublished bin
+    int32_t marks[3];       // look-back: nearest inclusive prefix / unpublished bin / gave up
     uint64_t bar;
     int64_t bin;
     int64_t prefix;
@@ -185,6 +184,9 @@ __device__ inline uint64_t warp_sum_u64(uint64_t v) {
 
 // Decoupled look-back, executed by one full warp.  Lane i inspects bin j - i,
 // so each poll covers 32 predecessors.  Returns the exclusive prefix.
+// Bounded: a lane gives up on a bin after SPIN_LIMIT polls, records
+// DEV_ERR_TIMEOUT and treats the bin as an inclusive prefix of 0, so the walk
+// always ends.
 __device__ inline int64_t lookback_warp(uint64_t *status, int64_t b, uint64_t agg, uint32_t *err) {
     const int lane = threadIdx.x & 31;
     if (b == 0) {
@@ -232,6 +234,11 @@ __device__ inline int64_t lookback_warp(uint64_t *status, int64_t b, uint64_t ag
 // (all threads); thread 0 publishes this bin's aggregate and inclusive prefix.
 // The chain starts at bin `first` (0 for one product; a product's first bin in
 // a batch): bins before it count as an inclusive prefix of 0.
+// Bounded: thread 0 waits at most SPIN_LIMIT polls in the whole look-back.
+// When that budget runs out it records DEV_ERR_TIMEOUT and the look-back stops
+// waiting: every bin still unpublished counts as 0 (its status word is 0), so
+// each later round either ends the walk or moves THREADS bins further back,
+// and the walk ends at bin `first` at the latest.
 template <int THREADS>
 __device__ inline int64_t lookback_block(uint64_t *status, int64_t b, uint64_t agg, uint32_t *err, int64_t *scratch,
                                          int32_t *marks, int64_t first) {
@@ -240,18 +247,23 @@ __device__ inline int64_t lookback_block(uint64_t *status, int64_t b, uint64_t a
         if (tid == 0) st_release_u64(&status[b], LB_PREFIX | agg);
         return 0;
     }
-    if (tid == 0) st_release_u64(&status[b], LB_AGGREGATE | agg);
+    if (tid == 0) {
+        st_release_u64(&status[b], LB_AGGREGATE | agg);
+        marks[2] = 0;  // set once the wait budget is spent
+    }
     uint64_t prefix = 0;
     int64_t j = b - 1;
     int64_t wait_for = b - 1;  // a bin whose count is needed and may be unpublished
+    uint32_t spins = 0;        // thread 0: polls so far in this look-back
     while (true) {
         // One lane waits (with backoff) until that bin has published; the other
         // threads sleep at the barrier instead of polling.
         if (tid == 0) {
-            uint32_t spins = 0, ns = 32;
-            while ((ld_acquire_u64(&status[wait_for]) >> LB_FLAG_SHIFT) == 0) {
+            uint32_t ns = 32;
+            while (marks[2] == 0 && (ld_acquire_u64(&status[wait_for]) >> LB_FLAG_SHIFT) == 0) {
                 if (++spins > SPIN_LIMIT) {
                     atomicOr(err, DEV_ERR_TIMEOUT);
+                    marks[2] = 1;
                     break;
                 }
                 __nanosleep(ns);
@@ -261,13 +273,14 @@ __device__ inline int64_t lookback_block(uint64_t *status, int64_t b, uint64_t a
             marks[1] = THREADS;  // nearest unpublished bin
         }
         __syncthreads();
+        const bool gave_up = marks[2] != 0;
         const int64_t idx = j - tid;
         const uint64_t v = (idx >= first) ? ld_acquire_u64(&status[idx]) : LB_PREFIX;  // before the chain: 0
         if ((v & ~LB_VALUE_MASK) == LB_PREFIX) atomicMin(&marks[0], tid);
         if ((v >> LB_FLAG_SHIFT) == 0) atomicMin(&marks[1], tid);
         __syncthreads();
         const int fp = marks[0], fz = marks[1];
-        if (fz < fp) {  // a bin in front of the nearest prefix has not published yet
+        if (fz < fp && !gave_up) {  // a bin in front of the nearest prefix has not published yet
             wait_for = j - fz;
             __syncthreads();
             continue;
@@ -344,10 +357,388 @@ __device__ void stream_oversize_bin(const NumericArgs &p, int64_t b, int32_t row
     __syncthreads();
 }
 
+// ---------------------------------------------------------------------------
+// Single-product sort kernel (one bin per CTA pass, bins taken by ticket).
+//
+// Phases of one bin of N <= CAP tuples (THREADS threads, E = CAP / THREADS
+// tuples per thread, bucket b = key >> shift with shift chosen so that the
+// bin's key range spans at most CAP buckets):
+//   A  count: thread t takes tuples t, t + THREADS, ...; one shared-memory
+//      atomic per tuple gives its bucket's count and its arrival rank there.
+//   B  bucket starts: thread t owns buckets [4t, 4t+4) and [CAP/2 + 4t, ...);
+//      both halves are scanned at once as the two 16-bit halves of one word
+//      (counts never exceed CAP <= 8192).  Each counter becomes the packed word
+//      start | size << 16, so one load later gives both.
+//   C  place: a tuple alone in its bucket is at its final position (its
+//      bucket's start); the others write (key bits below the bucket, position
+//      in the bin) into their bucket's slots.
+//   D  rank: a tuple of a multi-tuple bucket counts the smaller packed words
+//      of its bucket; equal keys order by position in the bin (a stable sort).
+//   A bucket above SMALL_BUCKET tuples switches the bin to a stable LSD radix
+//   sort (8-bit digits, warp multisplit ranking) instead of B-D.
+//   E  heads: warp w owns sorted positions [w*CAP/NW, (w+1)*CAP/NW) in
+//      32-position chunks; a head is a key different from its predecessor,
+//      one ballot per chunk marks them and the warp's count of merged entries
+//      goes to shared memory.  Warp 0 then publishes the bin's count and finds
+//      its prefix by the decoupled look-back.
+//   F  write C: the merged entry of a run goes to prefix + (heads before it).
+//      Chunks without duplicates write every tuple directly; a chunk with
+//      duplicates sums each run by a segmented warp-shuffle reduction
+//      (Sec. III-E's merge), or sequentially from its head when duplicates are
+//      few or the order of the sum is fixed (deterministic mode: equal keys
+//      then sum in position order, i.e. ascending k).  Row pointers are written
+//      where the row changes.
+// ---------------------------------------------------------------------------
+template <int CAP, int THREADS, class TV>
+struct BinSmem {
+    static constexpr int NW = THREADS / 32;
+    uint32_t kin[CAP];     // the bin's keys (bulk copy), then its sorted keys
+    TV vin[CAP];           // the bin's values (bulk copy)
+    uint32_t pk[CAP];      // multi-tuple buckets: low key bits << log2(CAP) | position; radix: keys
+    uint16_t fidx[CAP];    // position in the bin of each sorted tuple
+    uint16_t sidx2[CAP];   // radix: positions
+    uint32_t cnt[CAP];     // bucket counters, then start | size << 16; radix digit counters
+    int64_t scratch[40];
+    uint32_t wtot[NW];     // per warp: bucket-count sums (B), merged entries (E)
+    uint64_t bar;
+    int64_t bin;
+    int64_t prefix;
+    uint32_t big;
+    int32_t ok;
+};
+
+__device__ inline uint32_t lanemask_le() {
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_le;" : "=r"(m));
+    return m;
+}
+
+template <int CAP, int THREADS>
+__device__ inline void zero_counters(uint32_t *cnt) {
+    static_assert(CAP % (4 * THREADS) == 0, "whole uint4 per thread");
+#pragma unroll
+    for (int i = 4 * threadIdx.x; i < CAP; i += 4 * THREADS) *reinterpret_cast<uint4 *>(cnt + i) = make_uint4(0, 0, 0, 0);
+}
+
+// Bucket of a key.  Keys of a bin lie below rows << colbits, so key >> shift
+// is below CAP; the clamp only keeps a malformed key (a column of B outside
+// [0, n)) inside the counter array.
+__device__ inline uint32_t bucket_of(uint32_t key, int shift, int cap) { return min(key >> shift, (uint32_t)cap - 1u); }
+
+// Packed bucket words of 4 consecutive counters starting at offset `s`.
+__device__ inline uint4 bucket_words(uint4 c, uint32_t s) {
+    uint4 o;
+    o.x = s | (c.x << 16);
+    s += c.x;
+    o.y = s | (c.y << 16);
+    s += c.y;
+    o.z = s | (c.z << 16);
+    s += c.z;
+    o.w = s | (c.w << 16);
+    return o;
+}
+
+template <int CAP, int THREADS, class TV, class OV>
+__global__ void __launch_bounds__(THREADS, (THREADS <= 256 ? 4 : (THREADS <= 512 ? 2 : 1))) k_binsort(const NumericArgs p) {
+    using S = BinSmem<CAP, THREADS, TV>;
+    constexpr int NW = THREADS / 32;
+    constexpr int E = CAP / THREADS;  // tuples per thread in A-D
+    constexpr int WS = CAP / NW;      // sorted positions per warp in E-F
+    constexpr int CH = WS / 32;       // chunks per warp
+    constexpr int HALF = CAP / 2;
+    constexpr int LOG_CAP = (CAP == 2048) ? 11 : (CAP == 4096) ? 12 : 13;
+    static_assert((1 << LOG_CAP) == CAP && E == 8 && CH == 8 && 256 * NW == CAP, "layout");
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    S &sm = *reinterpret_cast<S *>(smem_raw);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const TV *__restrict__ gvals = static_cast<const TV *>(p.vals);
+    OV *__restrict__ valC = static_cast<OV *>(p.valC);
+    int32_t *__restrict__ colidxC = p.colidx;
+    const bool det = p.apos != nullptr;
+    const int colbits = p.colbits;
+    const uint32_t colmask = (colbits >= 32) ? 0xffffffffu : ((1u << colbits) - 1u);
+
+    if (tid == 0) {
+        mbar_init(&sm.bar, 1);
+        sm.big = 0;
+    }
+    zero_counters<CAP, THREADS>(sm.cnt);
+    uint32_t phase = 0;
+    while (true) {
+        if (tid == 0) sm.bin = p.bin_lo + (int64_t)atomicAdd(p.ticket, 1u);
+        fence_proxy_async_smem();  // this thread's reads of the last bin before the next bulk copy
+        __syncthreads();
+        const int64_t b = sm.bin;
+        if (b >= p.bin_hi) break;
+        const int32_t row0 = p.bin_row[b], row1 = p.bin_row[b + 1];
+        const int64_t off = p.bin_off[b] - p.tuple_base;  // the buffer holds this panel's tuples
+        const int64_t Nfull = p.R[row1] - p.R[row0];
+        if (Nfull > CAP) {
+            stream_oversize_bin<THREADS, TV, OV>(p, b, row0, row1, off, Nfull, colmask, sm.scratch, &sm.prefix,
+                                                 &sm.ok);
+            continue;
+        }
+        int N = (int)Nfull;
+        const int rows_b = row1 - row0;
+        // ---- load the bin (bulk copies, 16-byte granules) ---------------------------
+        bool loaded = true;
+        if (N > 0) {
+            if (tid == 0) {
+                const uint32_t n4 = (uint32_t)((N + 3) & ~3);
+                mbar_arrive_expect_tx(&sm.bar, n4 * 4u + n4 * (uint32_t)sizeof(TV));
+                bulk_g2s(sm.kin, p.keys + off, n4 * 4u, &sm.bar);
+                bulk_g2s(sm.vin, gvals + off, n4 * (uint32_t)sizeof(TV), &sm.bar);
+            }
+            loaded = mbar_wait_bounded(&sm.bar, phase);
+            phase ^= 1u;
+        }
+        if (!__syncthreads_and(loaded)) {
+            if (tid == 0) atomicOr(p.err, DEV_ERR_TIMEOUT);
+            // a bulk copy may still be landing: wait for it (bounded) before the buffer is reused
+            (void)mbar_wait_bounded(&sm.bar, phase ^ 1u);
+            N = 0;
+        }
+        const uint32_t *sk = sm.kin;   // sorted keys
+        const uint16_t *si = sm.fidx;  // their positions in the bin
+        if (N > 0) {
+            const uint32_t kmax = (uint32_t)((((uint64_t)rows_b) << colbits) - 1u);
+            const int rbits = kmax ? 32 - __clz(kmax) : 0;
+            const int shift = rbits > LOG_CAP ? rbits - LOG_CAP : 0;  // <= 32 - LOG_CAP
+            const uint32_t lowmask = (1u << shift) - 1u;
+            // ---- A: bucket counts and arrival ranks ------------------------------------
+            uint32_t kr[E], rk[E];
+            bool mine_big = false;
+#pragma unroll
+            for (int j = 0; j < E; ++j) {
+                const int q = tid + j * THREADS;
+                kr[j] = 0;
+                rk[j] = 0;
+                if (q < N) {
+                    kr[j] = sm.kin[q];
+                    rk[j] = atomicAdd(&sm.cnt[bucket_of(kr[j], shift, CAP)], 1u);
+                    mine_big |= rk[j] >= SMALL_BUCKET;
+                }
+            }
+            if (mine_big) sm.big = 1;
+            __syncthreads();
+            if (sm.big == 0) {
+                // ---- B: bucket starts ---------------------------------------------------
+                {
+                    uint4 *c0 = reinterpret_cast<uint4 *>(sm.cnt + 4 * tid);
+                    uint4 *c1 = reinterpret_cast<uint4 *>(sm.cnt + HALF + 4 * tid);
+                    const uint4 a0 = *c0, a1 = *c1;
+                    const uint32_t v = (a0.x + a0.y + a0.z + a0.w) | ((a1.x + a1.y + a1.z + a1.w) << 16);
+                    const uint32_t inc = warp_inclusive_scan(v);
+                    if (lane == 31) sm.wtot[warp] = inc;
+                    __syncthreads();
+                    uint32_t base = 0, total = 0;
+#pragma unroll
+                    for (int w = 0; w < NW; ++w) {
+                        const uint32_t t = sm.wtot[w];
+                        base += (w < warp) ? t : 0u;
+                        total += t;
+                    }
+                    const uint32_t ex = base + inc - v;
+                    *c0 = bucket_words(a0, ex & 0xffffu);
+                    *c1 = bucket_words(a1, (total & 0xffffu) + (ex >> 16));
+                }
+                __syncthreads();
+                // ---- C: singletons to their final slot, the rest into their bucket ------
+                uint32_t multi = 0;
+#pragma unroll
+                for (int j = 0; j < E; ++j) {
+                    const int q = tid + j * THREADS;
+                    if (q < N) {
+                        const uint32_t w = sm.cnt[bucket_of(kr[j], shift, CAP)];
+                        const uint32_t start = w & 0xffffu;
+                        if ((w >> 16) == 1u) {
+                            sm.kin[start] = kr[j];
+                            sm.fidx[start] = (uint16_t)q;
+                        } else {
+                            sm.pk[start + rk[j]] = ((kr[j] & lowmask) << LOG_CAP) | (uint32_t)q;
+                            multi |= 1u << j;
+                        }
+                    }
+                }
+                __syncthreads();
+                // ---- D: rank inside multi-tuple buckets ---------------------------------
+#pragma unroll
+                for (int j = 0; j < E; ++j) {
+                    if (multi & (1u << j)) {
+                        const int q = tid + j * THREADS;
+                        const uint32_t w = sm.cnt[bucket_of(kr[j], shift, CAP)];
+                        const int start = (int)(w & 0xffffu), end = start + (int)(w >> 16);
+                        const uint32_t mine = ((kr[j] & lowmask) << LOG_CAP) | (uint32_t)q;
+                        int rank = start;
+                        for (int r = start; r < end; ++r) rank += sm.pk[r] < mine;
+                        sm.kin[rank] = kr[j];
+                        sm.fidx[rank] = (uint16_t)q;
+                    }
+                }
+                __syncthreads();
+            } else {
+                // ---- stable LSD radix sort, 8-bit digits --------------------------------
+                const uint32_t *srck = sm.kin;
+                const uint16_t *srci = nullptr;  // identity on the first pass
+                uint32_t *dstk = sm.pk;
+                uint16_t *dsti = sm.fidx;
+                const int passes_bits = rbits > 0 ? rbits : 1;
+                for (int sh = 0; sh < passes_bits; sh += 8) {
+                    zero_counters<CAP, THREADS>(sm.cnt);
+                    __syncthreads();
+                    uint32_t kk[E], lr[E];
+                    uint16_t ii[E];
+                    uint8_t dd[E];
+#pragma unroll
+                    for (int j = 0; j < E; ++j) {
+                        const int q = warp * WS + j * 32 + lane;
+                        const bool valid = q < N;
+                        const uint32_t key = valid ? srck[q] : 0u;
+                        const uint32_t d = (key >> sh) & 255u;
+                        uint32_t peers = __ballot_sync(FULL, valid);
+#pragma unroll
+                        for (int bit = 0; bit < 8; ++bit) {
+                            const bool on = (d >> bit) & 1u;
+                            const uint32_t bb = __ballot_sync(FULL, on);
+                            peers &= on ? bb : ~bb;
+                        }
+                        const int leader = valid ? (__ffs(peers) - 1) : lane;
+                        uint32_t old = 0;
+                        if (valid && lane == leader) {
+                            old = sm.cnt[d * NW + warp];
+                            sm.cnt[d * NW + warp] = old + __popc(peers);
+                        }
+                        old = __shfl_sync(FULL, old, leader);
+                        __syncwarp();
+                        lr[j] = old + __popc(peers & lanemask_lt());
+                        kk[j] = key;
+                        ii[j] = valid ? (srci ? srci[q] : (uint16_t)q) : 0;
+                        dd[j] = (uint8_t)d;
+                    }
+                    __syncthreads();
+                    smem_exclusive_scan<THREADS>(sm.cnt, 256 * NW, sm.scratch);
+#pragma unroll
+                    for (int j = 0; j < E; ++j) {
+                        const int q = warp * WS + j * 32 + lane;
+                        if (q < N) {
+                            const uint32_t pos = sm.cnt[(uint32_t)dd[j] * NW + warp] + lr[j];
+                            dstk[pos] = kk[j];
+                            dsti[pos] = ii[j];
+                        }
+                    }
+                    __syncthreads();
+                    srck = dstk;
+                    srci = dsti;
+                    dstk = (dstk == sm.pk) ? sm.kin : sm.pk;
+                    dsti = (dsti == sm.fidx) ? sm.sidx2 : sm.fidx;
+                }
+                sk = srck;
+                si = srci;
+            }
+        }
+        // counters of the next bin (buckets and digits are no longer read)
+        zero_counters<CAP, THREADS>(sm.cnt);
+        if (tid == 0) sm.big = 0;
+        // ---- E: heads (first tuple of each run of equal keys), per warp segment --------
+        const int sbase = warp * WS;
+        const uint32_t before = (sbase > 0 && sbase - 1 < N) ? sk[sbase - 1] : 0u;  // key ahead of the segment
+        uint32_t keyc[CH], hmc[CH];
+        uint32_t heads = 0;
+        {
+            uint32_t last = before;
+#pragma unroll
+            for (int c = 0; c < CH; ++c) {
+                const int q = sbase + c * 32 + lane;
+                const bool valid = q < N;
+                const uint32_t key = valid ? sk[q] : 0u;
+                uint32_t prev = __shfl_up_sync(FULL, key, 1);
+                if (lane == 0) prev = last;
+                hmc[c] = __ballot_sync(FULL, valid && (q == 0 || key != prev));
+                heads += __popc(hmc[c]);
+                keyc[c] = key;
+                last = __shfl_sync(FULL, key, 31);
+            }
+        }
+        if (lane == 0) sm.wtot[warp] = heads;
+        __syncthreads();
+        int64_t U = 0, wbase = 0;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) {
+            const uint32_t t = sm.wtot[w];
+            wbase += (w < warp) ? t : 0u;
+            U += t;
+        }
+        if (warp == 0) publish_and_check(p, b, U, &sm.prefix, &sm.ok);
+        __syncthreads();
+        if (!sm.ok) continue;
+        // ---- F: merged entries and row pointers ---------------------------------------
+        const int64_t P = sm.prefix;
+        int64_t running = P + wbase;  // C position of the segment's first head
+        uint32_t last = before;
+#pragma unroll
+        for (int c = 0; c < CH; ++c) {
+            const int q = sbase + c * 32 + lane;
+            const bool valid = q < N;
+            const uint32_t vm = __ballot_sync(FULL, valid);
+            if (vm == 0) break;
+            const uint32_t key = keyc[c], hm = hmc[c];
+            uint32_t prev = __shfl_up_sync(FULL, key, 1);
+            if (lane == 0) prev = last;
+            last = __shfl_sync(FULL, key, 31);
+            const bool head = (hm >> lane) & 1u;
+            const int64_t idx = running + __popc(hm & lanemask_le()) - 1;  // this tuple's merged entry
+            if (head) {  // rows from the one after the previous tuple's row up to this row start here
+                const int rh = (int)(key >> colbits);
+                const int rp = (q == 0) ? -1 : (int)(prev >> colbits);
+                for (int r = rp + 1; r <= rh; ++r) write_rowptr(p, row0 + r, idx);
+            }
+            // does the run holding lane 31 end inside this chunk?
+            bool ends = true;
+            const int qn = sbase + c * 32 + 32;
+            if (vm == FULL && qn < N) ends = (c + 1 < CH) ? ((hmc[c + 1 < CH ? c + 1 : c] & 1u) != 0) : (sk[qn] != last);
+            const int dups = __popc(vm & ~hm);
+            if (hm == vm && ends) {
+                if (valid) {  // no duplicates: every tuple is its own entry
+                    colidxC[idx] = (int32_t)(key & colmask);
+                    valC[idx] = (OV)(double)sm.vin[si[q]];
+                }
+            } else if (det || dups <= 4) {
+                if (head) {  // the run summed in sorted order from its head
+                    double acc = (double)sm.vin[si[q]];
+                    for (int r = q + 1; r < N && sk[r] == key; ++r) acc += (double)sm.vin[si[r]];
+                    colidxC[idx] = (int32_t)(key & colmask);
+                    valC[idx] = (OV)acc;
+                }
+            } else {
+                // segmented suffix sums: lane l adds lanes (l, end of its run in the chunk]
+                double v = valid ? (double)sm.vin[si[q]] : 0.0;
+                const uint32_t after = hm & ~lanemask_le();
+                const int endl = after ? __ffs(after) - 2 : 31;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const double t = __shfl_down_sync(FULL, v, o);
+                    if (lane + o <= endl) v += t;
+                }
+                if (head) {
+                    if (endl == 31 && !ends)  // the run goes on past the chunk
+                        for (int r = qn; r < N && sk[r] == key; ++r) v += (double)sm.vin[si[r]];
+                    colidxC[idx] = (int32_t)(key & colmask);
+                    valC[idx] = (OV)v;
+                }
+            }
+            running += __popc(hm);
+        }
+        if (warp == 0) {  // rows after the bin's last tuple (all rows of an empty bin)
+            const int rl = N > 0 ? (int)(sk[N - 1] >> colbits) : -1;
+            for (int r = rl + 1 + lane; r < rows_b; r += 32) write_rowptr(p, row0 + r, P + U);
+        }
+    }
+}
+
 // BATCH: bins of the products of a batch that share one capacity level; each
 // bin writes into its own product's C (taken from the product's descriptor).
 template <int CAP, int THREADS, class TV, class OV, bool BATCH>
-__global__ void __launch_bounds__(THREADS, (THREADS <= 256 ? 4 : (THREADS <= 512 ? 2 : 1))) k_binsort(const NumericArgs p) {
+__global__ void __launch_bounds__(THREADS, (THREADS <= 256 ? 4 : (THREADS <= 512 ? 2 : 1))) k_binsort_batch(const NumericArgs p) {
     using S = SortSmem<CAP, THREADS, TV>;
     constexpr int NW = THREADS / 32;
     constexpr int E = CAP / THREADS;  // tuples per thread; also buckets per thread
@@ -673,9 +1064,8 @@ __global__ void __launch_bounds__(THREADS, (THREADS <= 256 ? 4 : (THREADS <= 512
 
 template <int CAP, int THREADS, class TV, class OV, bool BATCH>
 cudaError_t run_binsort(const NumericArgs &a, cudaStream_t s) {
-    using S = SortSmem<CAP, THREADS, TV>;
-    auto kern = k_binsort<CAP, THREADS, TV, OV, BATCH>;
-    const size_t smem = sizeof(S);
+    auto kern = BATCH ? k_binsort_batch<CAP, THREADS, TV, OV, true> : k_binsort<CAP, THREADS, TV, OV>;
+    const size_t smem = BATCH ? sizeof(SortSmem<CAP, THREADS, TV>) : sizeof(BinSmem<CAP, THREADS, TV>);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;

@@ -28,8 +28,12 @@ constexpr uint64_t LB_AGGREGATE = 1ull << LB_FLAG_SHIFT;
 constexpr uint64_t LB_PREFIX = 2ull << LB_FLAG_SHIFT;
 constexpr uint64_t LB_VALUE_MASK = (1ull << LB_FLAG_SHIFT) - 1;
 
-// Bounded spin: every device wait gives up after this many polls.
-constexpr uint32_t SPIN_LIMIT = 1u << 24;
+// Bounded spin: every device wait gives up after this many polls.  A test
+// build lowers it (PB_SPIN_LIMIT) to make a wait run out quickly.
+#ifndef PB_SPIN_LIMIT
+#define PB_SPIN_LIMIT (1u << 24)
+#endif
+constexpr uint32_t SPIN_LIMIT = PB_SPIN_LIMIT;
 
 // Tuples per work item of the oversize-bin sort.
 constexpr int OVER_CHUNK = 4096;
