@@ -45,6 +45,7 @@ struct pb_plan {
     size_t apos_bytes = 0;
     int64_t *F = nullptr, *R = nullptr, *flags = nullptr, *bin_off = nullptr, *scan_tmp = nullptr;
     uint64_t *rowinfo = nullptr, *ainfo = nullptr;
+    int2 *aspan = nullptr;
     int32_t *bin_row = nullptr, *chunk_e = nullptr, *acol = nullptr;
     PlanHeader *dhdr = nullptr;
     uint32_t *err = nullptr;
@@ -64,6 +65,12 @@ namespace {
 constexpr int32_t kVersion = 1 * 10000 + 0 * 100 + 0;
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// Bin cursors start at the bins' offsets, PB_CURSOR_STRIDE words apart.
+cudaError_t reset_cursors(void *cursor, const int64_t *bin_off, size_t nb, cudaStream_t s) {
+    if (nb == 0) return cudaSuccess;
+    return cudaMemcpy2DAsync(cursor, 8 * (size_t)PB_CURSOR_STRIDE, bin_off, 8, 8, nb, cudaMemcpyDeviceToDevice, s);
+}
 
 void *default_alloc(size_t bytes, pb_stream_t stream, void *) {
     void *p = nullptr;
@@ -235,6 +242,7 @@ pb_status pb_spgemm_symbolic(pb_handle *h, const pb_csc *A, const pb_csr *B, pb_
     const size_t oH = take(sizeof(PlanHeader)), oT = take(8 * scan_tmp_elems(scan_n)), oE = take(64);
     const size_t oOs = take(8 * (m + 1)), oOb = take(8 * (m + 1)), oOc = take(8 * (m + 1)), oOt = take(8 * (m + 1));
     const size_t oAi = take(8 * (p->nnzA > 0 ? p->nnzA : 1)), oAc = take(4 * (p->nnzA > 0 ? p->nnzA : 1));
+    const size_t oAs = take(8 * (p->nnzA > 0 ? p->nnzA : 1));
     const size_t oLc = take(4 * (k > 0 ? k : 1) + 256);
     p->arena_bytes = off;
     p->arena = h->alloc(p->arena_bytes, stream_, h->ctx);
@@ -258,6 +266,7 @@ pb_status pb_spgemm_symbolic(pb_handle *h, const pb_csc *A, const pb_csr *B, pb_
     p->over_tuple_off = reinterpret_cast<int64_t *>(base + oOt);
     p->ainfo = reinterpret_cast<uint64_t *>(base + oAi);
     p->acol = reinterpret_cast<int32_t *>(base + oAc);
+    p->aspan = reinterpret_cast<int2 *>(base + oAs);
 
     auto bail = [&](pb_status code) {
         free_plan_memory(p);
@@ -283,6 +292,7 @@ pb_status pb_spgemm_symbolic(pb_handle *h, const pb_csc *A, const pb_csr *B, pb_
     a.rowinfo = p->rowinfo;
     a.ainfo = p->ainfo;
     a.acol = p->acol;
+    a.aspan = p->aspan;
     a.long_cols = reinterpret_cast<int32_t *>(base + oLc);
     a.n_long = reinterpret_cast<uint32_t *>(base + oLc + 4 * (k > 0 ? k : 1));
     a.nnzA = p->nnzA;
@@ -463,7 +473,7 @@ pb_status pb_spgemm_symbolic(pb_handle *h, const pb_csc *A, const pb_csr *B, pb_
     p->ws_vals = w;
     w += align256(tuple_val_bytes(dtype) * T);
     p->ws_cursor = w;
-    w += align256(8 * nb);
+    w += align256(8 * (size_t)PB_CURSOR_STRIDE * nb);
     p->ws_status = w;
     w += align256(8 * nb);
     p->ws_ctrl = w;
@@ -525,6 +535,7 @@ static pb_status fill_numeric(pb_handle *h, const pb_plan *p, const pb_csc *A, c
     a.bin_off = p->bin_off;
     a.chunk_e = p->chunk_e;
     a.acol = p->acol;
+    a.aspan = p->aspan;
     a.apos = static_cast<const int64_t *>(p->apos_mem);
     a.flop = p->hdr.flop;
     a.nbins = p->hdr.nbins;
@@ -534,9 +545,11 @@ static pb_status fill_numeric(pb_handle *h, const pb_plan *p, const pb_csc *A, c
     a.capacity = p->capacity;
     a.keys = reinterpret_cast<uint32_t *>(w + p->ws_keys);
     a.cursor = reinterpret_cast<uint64_t *>(w + p->ws_cursor);
+    a.cursor_stride = PB_CURSOR_STRIDE;
     a.vals = w + p->ws_vals;
     a.status = reinterpret_cast<uint64_t *>(w + p->ws_status);
     a.ticket = reinterpret_cast<uint32_t *>(w + p->ws_ctrl);
+    a.work = reinterpret_cast<uint32_t *>(w + p->ws_ctrl) + 32;  // words 16, 17: oversize row tickets
     a.err = p->err;
     a.dtype = p->dtype;
     a.num_sms = h->num_sms;
@@ -618,7 +631,7 @@ static pb_status run_numeric(pb_handle *h, const pb_plan *p, const pb_csc *A, co
         if (C->nnz_dev) PB_CUDA(h, cudaMemsetAsync(C->nnz_dev, 0, 8, s));
         return PB_OK;
     }
-    PB_CUDA(h, cudaMemcpyAsync(w + p->ws_cursor, p->bin_off, 8 * nb, cudaMemcpyDeviceToDevice, s));
+    PB_CUDA(h, reset_cursors(w + p->ws_cursor, p->bin_off, nb, s));
     PB_CUDA(h, cudaMemsetAsync(w + p->ws_status, 0, 8 * nb, s));  // look-back words: all panels
     if (h->phase_on) PB_CUDA(h, cudaEventRecord(h->phase_ev[1], s));
     const bool single = p->panels.size() == 1;
@@ -839,7 +852,8 @@ pb_status pb_debug_expand(pb_handle *h, const pb_plan *p, const pb_csc *A, const
     a.bin_hi = pn.bin_hi;
     a.tuple_base = pn.tuple_base;
     a.over_base = pn.over_base;
-    PB_CUDA(h, cudaMemcpyAsync(w + p->ws_cursor, p->bin_off, 8 * (size_t)p->hdr.nbins, cudaMemcpyDeviceToDevice, s));
+    PB_CUDA(h, reset_cursors(w + p->ws_cursor, p->bin_off, (size_t)p->hdr.nbins, s));
+    PB_CUDA(h, cudaMemsetAsync(w + p->ws_ctrl, 0, 256, s));
     PB_CUDA(h, launch_expand(a, s));
     return PB_OK;
 }

@@ -67,6 +67,7 @@ struct BatchWs {
     int64_t *F, *R, *flags;
     uint64_t *rowinfo, *ainfo;
     int32_t *acol;
+    int2 *aspan;
     int64_t *long_cols;
     int32_t *bin_row, *bin_prod;
     int64_t *bin_off;
@@ -111,6 +112,7 @@ size_t carve_fixed(BatchWs &w, char *base, int32_t count, int64_t M, int64_t K, 
     w.rowinfo = c.take<uint64_t>(8 * (size_t)M);
     w.ainfo = c.take<uint64_t>(8 * (size_t)E);
     w.acol = c.take<int32_t>(4 * (size_t)E);
+    w.aspan = c.take<int2>(8 * (size_t)E);
     w.long_cols = c.take<int64_t>(8 * (size_t)K);
     w.bin_row = c.take<int32_t>(4 * ((size_t)M + 2));
     w.bin_prod = c.take<int32_t>(4 * ((size_t)M + 2));
@@ -445,7 +447,7 @@ __global__ void __launch_bounds__(T) k_bentry(int32_t count, const BatchDesc *__
                                               const int32_t *__restrict__ tiles_e, const int32_t *__restrict__ acol,
                                               const uint64_t *__restrict__ rowinfo, const int64_t *__restrict__ F,
                                               const BatchProd *__restrict__ prod, const uint32_t *err,
-                                              uint64_t *ainfo, int32_t *chunk_e, int32_t *chunk_prod) {
+                                              uint64_t *ainfo, int2 *aspan, int32_t *chunk_e, int32_t *chunk_prod) {
     if (*err & DEV_ERR_BATCH_FATAL) return;
     const int64_t ntiles = tiles_e[count];
     for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
@@ -462,6 +464,7 @@ __global__ void __launch_bounds__(T) k_bentry(int32_t count, const BatchDesc *__
             ainfo[eg] = rowinfo[d.mstart + d.rowidxA[e]];
             const int32_t kk = acol[eg];
             const int64_t lb = (int64_t)d.rowptrB[kk + 1] - d.rowptrB[kk];
+            aspan[eg] = make_int2(d.rowptrB[kk], (int32_t)lb);
             if (lb == 0) continue;
             const int64_t s = (F[d.kstart + kk] - F0) + (e - d.colptrA[kk]) * lb, r = s + lb;
             for (int64_t c = ceil_div<int64_t>(s, chunk); c * chunk < r; ++c) {
@@ -693,7 +696,7 @@ pb_status launch_batch(pb_handle *h, const BatchHost &bh, const BatchWs &w, pb_d
                                                          w.bin_off, w.cursor, w.status, w.err);
         // 5. per A entry: bin info and expand work items
         k_bentry<<<grid_cap(bh.tiles_total[2], 1, cap), T, 0, s>>>(count, w.desc, w.tiles_e, w.acol, w.rowinfo,
-                                                                   w.F, w.prod, w.err, w.ainfo, w.chunk_e,
+                                                                   w.F, w.prod, w.err, w.ainfo, w.aspan, w.chunk_e,
                                                                    w.chunk_prod);
         count_launches(4);
         PB_CUDA_H(h, cudaGetLastError());
@@ -701,6 +704,7 @@ pb_status launch_batch(pb_handle *h, const BatchHost &bh, const BatchWs &w, pb_d
         NumericArgs a{};
         a.ainfo = w.ainfo;
         a.acol = w.acol;
+        a.aspan = w.aspan;
         a.bin_row = w.bin_row;
         a.bin_off = w.bin_off;
         a.R = w.R;
@@ -712,6 +716,7 @@ pb_status launch_batch(pb_handle *h, const BatchHost &bh, const BatchWs &w, pb_d
         a.keys = w.keys;
         a.vals = w.vals;
         a.cursor = w.cursor;
+        a.cursor_stride = 1;
         a.status = w.status;
         a.err = w.err;
         a.dtype = dtype;
@@ -721,6 +726,7 @@ pb_status launch_batch(pb_handle *h, const BatchHost &bh, const BatchWs &w, pb_d
         a.bin_prod = w.bin_prod;
         a.prod = w.prod;
         a.bhdr = w.bhdr;
+        a.work = w.err + 32;  // the control block is zeroed at the start of the call
         if (h->phase_on) PB_CUDA_H(h, cudaEventRecord(h->phase_ev[1], s));
         PB_CUDA_H(h, launch_expand_batch(a, s));
         if (h->phase_on) PB_CUDA_H(h, cudaEventRecord(h->phase_ev[2], s));

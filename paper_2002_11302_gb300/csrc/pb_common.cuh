@@ -35,6 +35,11 @@ constexpr uint64_t LB_VALUE_MASK = (1ull << LB_FLAG_SHIFT) - 1;
 #endif
 constexpr uint32_t SPIN_LIMIT = PB_SPIN_LIMIT;
 
+// Words between two bins' expand cursors in a single product's workspace.
+#ifndef PB_CURSOR_STRIDE
+#define PB_CURSOR_STRIDE 1
+#endif
+
 // Tuples per work item of the oversize-bin sort.
 constexpr int OVER_CHUNK = 4096;
 
@@ -64,6 +69,7 @@ struct SymbolicArgs {
     uint64_t *rowinfo;   // [m]   (bin << 32) | (local_row << colbits)
     uint64_t *ainfo;     // [nnzA] rowinfo of each A entry's row
     int32_t *acol;       // [nnzA] column of each A entry
+    int2 *aspan;         // [nnzA] B(k,:) of each A entry (column k): (first entry, length)
     int32_t *long_cols;  // [k] scratch: columns with many entries
     uint32_t *n_long;    // [1] scratch counter
     int64_t nnzA;
@@ -311,6 +317,7 @@ struct NumericArgs {
     const int64_t *F, *R;
     const uint64_t *ainfo;  // [nnzA] bin << 32 | key high part, per A entry
     const int32_t *acol;    // [nnzA] column of each A entry
+    const int2 *aspan;      // [nnzA] B(k,:) of each A entry: (first entry, length)
     const int32_t *bin_row;
     const int64_t *bin_off;
     const int32_t *chunk_e; // [nchunks+1] first A entry of each expand work item
@@ -323,9 +330,11 @@ struct NumericArgs {
     // workspace
     uint32_t *keys;
     void *vals;
-    uint64_t *cursor;    // [nbins] next free absolute slot of each bin
+    uint64_t *cursor;    // [nbins * cursor_stride] next free absolute slot of bin b at cursor[b * cursor_stride]
+    int32_t cursor_stride;  // words between two bins' cursors (spreads the atomics over cache lines)
     uint64_t *status;    // [nbins] look-back words
     uint32_t *ticket;    // [1]
+    uint32_t *work;      // [1] expand work items taken so far (zeroed before the expand)
     uint32_t *err;       // [1] device status word
     // output
     int64_t *rowptr64;

@@ -120,7 +120,7 @@ extern "C" pb_status pb_spgemm_noalloc(const pb_csc *A, const pb_csr *B, pb_dtyp
               cv.take(a.over_scan, 8 * m1) && cv.take(a.over_bin, 8 * m1) && cv.take(a.over_chunk_off, 8 * m1) &&
               cv.take(a.over_tuple_off, 8 * m1) && cv.take(a.ainfo, 8 * (nnzA > 0 ? (size_t)nnzA : 1));
     ok = ok && cv.take(acol, 4 * (nnzA > 0 ? (size_t)nnzA : 1)) && cv.take(a.long_cols, 4 * (k > 0 ? (size_t)k : 1)) &&
-         cv.take(a.n_long, 4);
+         cv.take(a.n_long, 4) && cv.take(a.aspan, 8 * (nnzA > 0 ? (size_t)nnzA : 1));
     if (!ok) return PB_ERR_WORKSPACE;  // the product needs more than the scratch array holds
 
     a.m = m;
@@ -187,6 +187,7 @@ extern "C" pb_status pb_spgemm_noalloc(const pb_csc *A, const pb_csr *B, pb_dtyp
     na.R = a.R;
     na.ainfo = a.ainfo;
     na.acol = acol;
+    na.aspan = a.aspan;
     na.bin_row = a.bin_row;
     na.bin_off = a.bin_off;
     na.chunk_e = chunk_e;
@@ -205,6 +206,7 @@ extern "C" pb_status pb_spgemm_noalloc(const pb_csc *A, const pb_csr *B, pb_dtyp
     na.nnz_dev = C->nnz_dev;
     na.cap = C->cap;
     na.count_only = 0;
+    na.cursor_stride = 1;
     na.dtype = dtype;
     int dev = 0;
     PB_NA_CUDA(cudaGetDevice(&dev));
@@ -230,6 +232,7 @@ extern "C" pb_status pb_spgemm_noalloc(const pb_csc *A, const pb_csr *B, pb_dtyp
     PB_NA_CUDA(cudaMemcpyAsync(na.cursor, a.bin_off, 8 * nb, cudaMemcpyDeviceToDevice, s));
     PB_NA_CUDA(cudaMemsetAsync(na.status, 0, 8 * nb, s));
     PB_NA_CUDA(cudaMemsetAsync(na.ticket, 0, 256, s));
+    na.work = na.ticket + 32;
     PB_NA_CUDA(launch_expand(na, s));
     if (hdr.n_oversize > 0) {
         OversizeArgs o{};

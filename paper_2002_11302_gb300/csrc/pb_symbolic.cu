@@ -190,9 +190,10 @@ __global__ void k_over_chunk_map(const int64_t *over_chunk_off, int64_t n_over, 
 //   entries tile [0, flop) in CSC order: entry j of column k owns
 //   [F[k] + j*lb, F[k] + (j+1)*lb) with lb = nnz(B(k,:)).  Work item c holds the
 //   entries whose run starts in [c*chunk, (c+1)*chunk): chunk_e[c] is the first.
-__device__ inline void entry_info(int64_t e, int64_t s, int64_t lb, int64_t chunk, const int32_t *rowidxA,
-                                  const uint64_t *rowinfo, uint64_t *ainfo, int32_t *chunk_e) {
+__device__ inline void entry_info(int64_t e, int64_t s, int32_t b0, int64_t lb, int64_t chunk, const int32_t *rowidxA,
+                                  const uint64_t *rowinfo, uint64_t *ainfo, int2 *aspan, int32_t *chunk_e) {
     ainfo[e] = rowinfo[rowidxA[e]];
+    aspan[e] = make_int2(b0, (int32_t)lb);
     if (lb == 0) return;
     const int64_t r = s + lb;
     for (int64_t c = ceil_div<int64_t>(s, chunk); c * chunk < r; ++c)
@@ -202,21 +203,22 @@ __device__ inline void entry_info(int64_t e, int64_t s, int64_t lb, int64_t chun
 // One thread per short column (the columns of the flop pass): its entries'
 // runs start at F[k], F[k] + lb, ...
 __global__ void k_entry_pass(int32_t k, const int32_t *colptrA, const int32_t *rowidxA, const int32_t *rowptrB,
-                             const uint64_t *rowinfo, const int64_t *F, int64_t chunk, uint64_t *ainfo,
+                             const uint64_t *rowinfo, const int64_t *F, int64_t chunk, uint64_t *ainfo, int2 *aspan,
                              int32_t *chunk_e) {
     for (int64_t col = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; col < k; col += (int64_t)gridDim.x * blockDim.x) {
         const int32_t a0 = colptrA[col], a1 = colptrA[col + 1];
         if (a1 - a0 > LONG_COL) continue;
         const int64_t lb = (int64_t)rowptrB[col + 1] - rowptrB[col];
         const int64_t s0 = F[col];
-        for (int32_t e = a0; e < a1; ++e) entry_info(e, s0 + (e - a0) * lb, lb, chunk, rowidxA, rowinfo, ainfo, chunk_e);
+        for (int32_t e = a0; e < a1; ++e)
+            entry_info(e, s0 + (e - a0) * lb, rowptrB[col], lb, chunk, rowidxA, rowinfo, ainfo, aspan, chunk_e);
     }
 }
 
 // One warp per listed long column.
 __global__ void k_entry_long(const int32_t *colptrA, const int32_t *rowidxA, const int32_t *rowptrB,
                              const uint64_t *rowinfo, const int64_t *F, const int32_t *long_cols,
-                             const uint32_t *n_long, int64_t chunk, uint64_t *ainfo, int32_t *chunk_e) {
+                             const uint32_t *n_long, int64_t chunk, uint64_t *ainfo, int2 *aspan, int32_t *chunk_e) {
     const int lane = threadIdx.x & 31;
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -226,7 +228,8 @@ __global__ void k_entry_long(const int32_t *colptrA, const int32_t *rowidxA, con
         const int32_t a0 = colptrA[col], a1 = colptrA[col + 1];
         const int64_t lb = (int64_t)rowptrB[col + 1] - rowptrB[col];
         const int64_t s0 = F[col];
-        for (int32_t e = a0 + lane; e < a1; e += 32) entry_info(e, s0 + (e - a0) * lb, lb, chunk, rowidxA, rowinfo, ainfo, chunk_e);
+        for (int32_t e = a0 + lane; e < a1; e += 32)
+            entry_info(e, s0 + (e - a0) * lb, rowptrB[col], lb, chunk, rowidxA, rowinfo, ainfo, aspan, chunk_e);
     }
 }
 
@@ -308,9 +311,10 @@ cudaError_t launch_chunk_table(const SymbolicArgs &a, int64_t nchunks, int64_t c
     count_launches(1);
     if (a.nnzA > 0) {
         k_entry_pass<<<grid_for(a.k, 256), 256, 0, s>>>(a.k, a.colptrA, a.rowidxA, a.rowptrB, a.rowinfo, a.F, chunk,
-                                                        a.ainfo, chunk_e);
+                                                        a.ainfo, a.aspan, chunk_e);
         k_entry_long<<<grid_for((int64_t)a.k * 32, 256), 256, 0, s>>>(a.colptrA, a.rowidxA, a.rowptrB, a.rowinfo, a.F,
-                                                                      a.long_cols, a.n_long, chunk, a.ainfo, chunk_e);
+                                                                      a.long_cols, a.n_long, chunk, a.ainfo, a.aspan,
+                                                                      chunk_e);
         count_launches(2);
     }
     return cudaGetLastError();
