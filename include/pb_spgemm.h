@@ -413,8 +413,11 @@ pb_status pb_serve_stats(pb_server *s, int64_t *completed, int64_t *preempted, s
  *   once at the end) and stores the device-detected status (PB_OK,
  *   PB_ERR_OVERFLOW, ...) in *device_status.
  *   The first call on a device resolves the scratch array's device address
- *   (cudaGetSymbolAddress, with that device current); make that first call
- *   before any stream capture.
+ *   (cudaGetSymbolAddress, with that device current) and keeps it for the
+ *   life of the process; make that first call before any stream capture.
+ *   Calls after a reset of the device (cudaDeviceReset) are not supported:
+ *   the kept address belongs to the context the reset destroyed.
+ *   *device_status uses the same mapping as pb_plan_status.
  *   All calls share the one array and it keeps the last call's contents (the
  *   call clears what it needs).  Calls whose work overlaps on the GPU, e.g.
  *   issued on two streams, race on the array: serialise them.

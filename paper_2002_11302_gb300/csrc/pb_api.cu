@@ -867,14 +867,7 @@ pb_status pb_plan_status(const pb_plan *p, pb_stream_t stream_, pb_status *devic
     cudaError_t e = cudaStreamSynchronize(s);
     if (e == cudaSuccess) e = cudaMemcpy(&word, p->err, 4, cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_fail(p->h, e, "plan status");
-    if (word & DEV_ERR_OVERFLOW)
-        *device_status = PB_ERR_OVERFLOW;
-    else if (word & DEV_ERR_TIMEOUT)
-        *device_status = PB_ERR_TIMEOUT;
-    else if (word & DEV_ERR_CAPACITY)
-        *device_status = PB_ERR_UNSUPPORTED;
-    else
-        *device_status = PB_OK;
+    *device_status = status_of_word(word);
     return PB_OK;
 }
 

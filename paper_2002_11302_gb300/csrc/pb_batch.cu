@@ -476,21 +476,7 @@ __global__ void __launch_bounds__(T) k_bentry(int32_t count, const BatchDesc *__
 }
 
 // The batch's status word, mapped to pb_status, in stream order after the sort.
-__global__ void k_bfinish(const uint32_t *err, int32_t *device_status) {
-    const uint32_t w = *err;
-    int32_t st = PB_OK;
-    if (w & DEV_ERR_HEAVY_ROW)
-        st = PB_ERR_UNSUPPORTED;
-    else if (w & DEV_ERR_WORKSPACE)
-        st = PB_ERR_WORKSPACE;
-    else if (w & DEV_ERR_OVERFLOW)
-        st = PB_ERR_OVERFLOW;
-    else if (w & DEV_ERR_TIMEOUT)
-        st = PB_ERR_TIMEOUT;
-    else if (w & DEV_ERR_CAPACITY)
-        st = PB_ERR_UNSUPPORTED;
-    *device_status = st;
-}
+__global__ void k_bfinish(const uint32_t *err, int32_t *device_status) { *device_status = status_of_word(*err); }
 
 unsigned grid_cap(int64_t n, int threads, int64_t cap) {
     int64_t g = ceil_div<int64_t>(n > 0 ? n : 1, threads);

@@ -22,6 +22,17 @@ enum : uint32_t {
 // Errors after which the batched kernels do no further work.
 constexpr uint32_t DEV_ERR_BATCH_FATAL = DEV_ERR_WORKSPACE | DEV_ERR_HEAVY_ROW;
 
+// The pb_status a device status word reports (one mapping for every entry
+// point): errors that stop the work first, then overflow, timeout, capacity.
+__host__ __device__ inline pb_status status_of_word(uint32_t w) {
+    if (w & DEV_ERR_HEAVY_ROW) return PB_ERR_UNSUPPORTED;
+    if (w & DEV_ERR_WORKSPACE) return PB_ERR_WORKSPACE;
+    if (w & DEV_ERR_OVERFLOW) return PB_ERR_OVERFLOW;
+    if (w & DEV_ERR_TIMEOUT) return PB_ERR_TIMEOUT;
+    if (w & DEV_ERR_CAPACITY) return PB_ERR_UNSUPPORTED;  // operands differ from the plan's structure
+    return PB_OK;
+}
+
 // Look-back status of one bin: two flag bits over a 62-bit count.
 constexpr uint64_t LB_FLAG_SHIFT = 62;
 constexpr uint64_t LB_AGGREGATE = 1ull << LB_FLAG_SHIFT;

@@ -264,11 +264,6 @@ extern "C" pb_status pb_spgemm_noalloc(const pb_csc *A, const pb_csr *B, pb_dtyp
     uint32_t word = 0;
     PB_NA_CUDA(cudaMemcpyAsync(&word, err, 4, cudaMemcpyDeviceToHost, s));
     PB_NA_CUDA(cudaStreamSynchronize(s));
-    if (word & DEV_ERR_OVERFLOW)
-        *device_status = PB_ERR_OVERFLOW;
-    else if (word & DEV_ERR_TIMEOUT)
-        *device_status = PB_ERR_TIMEOUT;
-    else if (word & DEV_ERR_CAPACITY)
-        *device_status = PB_ERR_UNSUPPORTED;
+    *device_status = status_of_word(word);  // the mapping pb_plan_status uses
     return PB_OK;
 }

@@ -354,17 +354,26 @@ def test_plan_reuse_with_new_values(pb):
 
 
 @pytest.mark.slow
-def test_er_full_size_sampled_rows(pb):
-    """The bench workload (ER n=2^21, d=8) in the bench's launch configuration."""
+def test_er_full_size_all_rows(pb):
+    """The bench workload (ER n=2^21, d=8, FP64) in the bench's launch
+    configuration, every entry of C against the full oracle product."""
     n, d = 1 << 21, 8
     A, B = synth.er(n, d, seed=1)
     C = run(pb, A, B)
     assert_csr_valid(C, n)
-    rows = np.random.default_rng(0).choice(n, 2000, replace=False)
-    rows = np.concatenate([rows, [0, n - 1]])
-    assert_rows_match(C, oracle.spgemm(A, B, rows), EPS["f64"])
-    nnz = int(C.rowptr[-1].item())
-    assert nnz <= n * d * d
+    assert_matches(C, oracle.spgemm(A, B), EPS["f64"])
+    assert int(C.rowptr[-1].item()) <= n * d * d
+
+
+def test_er22_fp32_tuples_full_size(pb):
+    """The mixed-precision configuration (ER n=2^22, d=8): FP64 inputs, products
+    rounded to FP32 in the tuples, merged in FP64; every entry of C against the
+    full FP64 oracle product with the FP32 rounding bound, structure exact."""
+    n, d = 1 << 22, 8
+    A, B = synth.er(n, d, seed=4)
+    C = run(pb, A, B, dtype=pb.PB_F64_F32TUPLE)
+    assert C.val.dtype == torch.float64
+    assert_matches(C, oracle.spgemm(A, B), EPS["f32"])
 
 
 @pytest.mark.parametrize("budget_tuples", [20000, 60000])

@@ -4,10 +4,12 @@ Callers whose device memory is owned by their own memory manager, or that run
 in loops or callbacks where entering an allocator is not allowed, cannot let
 the library call cudaMalloc.  pb_spgemm_noalloc serves them from a fixed
 scratch array inside the library.  These tests call it through the C ABI and
-compare its result with the regular entry points (pb_spgemm_symbolic +
-pb_spgemm_numeric) on two calls in a row, with the same tolerance as the other
-parity tests; the array keeps the previous call's contents, so the second call
-also checks that nothing stale leaks into a result.
+compare its result with the CPU oracle (structure exactly, values within
+64 * eps * sum |a b| for the dtype's rounding) on two calls in a row: the array
+keeps the previous call's contents, so the second call also checks that
+nothing stale leaks into a result.  They cover FP64, FP32 and FP32 tuples,
+inputs with rows above the on-chip bin capacity (R-MAT hub rows, merged by the
+global radix sort), and int32 row pointers.
 
 This file is named to be collected last.
 """
@@ -35,53 +37,57 @@ def _flop(A, B) -> int:
     return int((np.diff(A.colptr).astype(np.int64) * np.diff(B.rowptr).astype(np.int64)).sum())
 
 
-def _run_noalloc(pb, A, B):
-    Ad, Bd = pb.csc_to_device(A), pb.csr_to_device(B)
+def _run_noalloc(pb, A, B, dtype, rowptr64=True):
+    vdt = torch.float32 if dtype == pb.PB_F32 else torch.float64
+    Ad, Bd = pb.csc_to_device(A, val_dtype=vdt), pb.csr_to_device(B, val_dtype=vdt)
     cap = max(_flop(A, B), 1)
-    C = pb.CsrMatrix(A.nrows, B.ncols, torch.empty(A.nrows + 1, dtype=torch.int64, device="cuda"),
-                     torch.empty(cap, dtype=torch.int32, device="cuda"),
-                     torch.empty(cap, dtype=torch.float64, device="cuda"))
+    C = pb.CsrMatrix(A.nrows, B.ncols,
+                     torch.empty(A.nrows + 1, dtype=torch.int64 if rowptr64 else torch.int32, device="cuda"),
+                     torch.empty(cap, dtype=torch.int32, device="cuda"), torch.empty(cap, dtype=vdt, device="cuda"))
     nnz = torch.zeros(1, dtype=torch.int64, device="cuda")
-    status = pb.spgemm_noalloc(Ad, Bd, C, nnz_out=nnz)
+    status = pb.spgemm_noalloc(Ad, Bd, C, dtype=dtype, nnz_out=nnz)
     assert status == 0, f"device status {status}"
     k = int(nnz.item())
-    assert k == int(C.rowptr[-1].item())
-    return C.rowptr.cpu().numpy(), C.colidx[:k].cpu().numpy(), C.val[:k].cpu().numpy()
+    rowptr = C.rowptr.cpu().numpy().astype(np.int64)
+    assert k == int(rowptr[-1])
+    return rowptr, C.colidx[:k].cpu().numpy(), C.val[:k].double().cpu().numpy()
 
 
-def _run_regular(pb, A, B):
-    C = pb.spgemm(pb.csc_to_device(A), pb.csr_to_device(B))
-    return C.rowptr.cpu().numpy(), C.colidx.cpu().numpy(), C.val.cpu().numpy()
+def _matches_oracle(got, ref, eps):
+    assert np.array_equal(got[0], ref.rowptr), "row pointers differ from the oracle"
+    assert np.array_equal(got[1], ref.colidx), "column indices differ from the oracle"
+    err = np.abs(got[2] - ref.val)
+    assert np.all(err <= TOL_FACTOR * eps * ref.absval), f"values outside the bound (max {err.max():.3e})"
 
 
-def _same(got, ref, scale):
-    assert np.array_equal(got[0], ref[0]), "row pointers differ"
-    assert np.array_equal(got[1], ref[1]), "column indices differ"
-    # both results lie within 64 eps sum|a b| of the exact product, hence of each other within twice that
-    assert np.all(np.abs(got[2] - ref[2]) <= 2 * TOL_FACTOR * EPS["f64"] * scale)
+CASES = [  # (name, inputs, dtype name, eps key)
+    ("er_f64", lambda: synth.er(6000, 6, seed=71), "PB_F64", "f64"),
+    ("rmat_hubs_f64", lambda: synth.rmat(11, 4, seed=72), "PB_F64", "f64"),
+    ("rmat_hubs_f32", lambda: synth.rmat(11, 4, seed=73, dtype=np.float32), "PB_F32", "f32"),
+    ("rmat_hubs_f32tuple", lambda: synth.rmat(11, 4, seed=74), "PB_F64_F32TUPLE", "f32"),
+]
 
 
-def test_noalloc_matches_regular_entry_points_on_two_calls(pb):
-    problems = [synth.er(6000, 6, seed=71), synth.rmat(11, 4, seed=72)]  # the second has oversize rows
-    for A, B in problems:
-        ref = _run_regular(pb, A, B)
-        scale = oracle.spgemm(A, B).absval
-        got = _run_noalloc(pb, A, B)
-        _same(got, ref, scale)
+@pytest.mark.parametrize("name,make,dtype,eps", CASES, ids=[c[0] for c in CASES])
+def test_noalloc_matches_oracle_on_two_calls(pb, name, make, dtype, eps):
+    A, B = make()
+    ref = oracle.spgemm(A, B)
+    if name.startswith("rmat"):  # the case must exercise rows above the on-chip capacity
+        assert int(oracle.row_flop(A, B).max()) > 4096
+    for _ in range(2):
+        _matches_oracle(_run_noalloc(pb, A, B, getattr(pb, dtype)), ref, EPS[eps])
 
 
-def test_noalloc_repeated_call_same_result(pb):
-    A, B = synth.er(4096, 4, seed=0)
-    first = _run_noalloc(pb, A, B)
-    second = _run_noalloc(pb, A, B)
-    assert np.array_equal(first[0], second[0]) and np.array_equal(first[1], second[1])
-    scale = oracle.spgemm(A, B).absval
-    assert np.all(np.abs(first[2] - second[2]) <= 2 * TOL_FACTOR * EPS["f64"] * scale)
+def test_noalloc_int32_row_pointers(pb):
+    A, B = synth.er(5000, 5, seed=75)
+    ref = oracle.spgemm(A, B)
+    for _ in range(2):
+        _matches_oracle(_run_noalloc(pb, A, B, pb.PB_F64, rowptr64=False), ref, EPS["f64"])
 
 
 def test_noalloc_rejects_products_above_its_scratch(pb):
     from paper_2002_11302_gb300 import binding
     A, B = synth.er(1 << 17, 8, seed=73)   # about 8.4M tuples: more than the fixed scratch holds
     with pytest.raises(binding.PBError) as ei:
-        _run_noalloc(pb, A, B)
+        _run_noalloc(pb, A, B, pb.PB_F64)
     assert ei.value.status == 10           # PB_ERR_WORKSPACE
