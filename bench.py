@@ -49,6 +49,11 @@ WORKLOADS = {
                             "FP32 tuples merged in FP64, row panels"),
     "er22": dict(kind="er", n=1 << 22, d=8, seed=4, dtype="f64",
                  desc="ER C=A*A, n=2^22, d=8 per column, FP64 values U(-1,1), int32 indices"),
+    "rmat21f32t": dict(kind="rmat", scale=21, ef=16, seed=5, dtype="f64_f32tuple", budget=64 << 30, count_only=True,
+                       desc="R-MAT C=A*A, scale 21, edge factor 16, (0.57,0.19,0.19,0.05), dedup, FP64 values, "
+                            "FP32 tuples merged in FP64, row panels; counting run: every tuple phase (expand, hub-row "
+                            "merge, bin sort and merge) runs, only C's entries are not written (C holds about 4e10 "
+                            "entries, more than the device or a flop-sized buffer can hold)"),
     "er22f32t": dict(kind="er", n=1 << 22, d=8, seed=4, dtype="f64_f32tuple",
                      desc="ER C=A*A, n=2^22, d=8, FP64 values, FP32 tuples merged in FP64, int32 indices"),
     "er19": dict(kind="er", n=1 << 19, d=8, seed=7, dtype="f64",
@@ -138,7 +143,7 @@ class ClockSampler:
     def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "50"],
+                                          "--format=csv,noheader,nounits", "-lms", "10"],
                                          stdout=self.out, stderr=subprocess.DEVNULL)
         except (FileNotFoundError, OSError):
             self.proc = None
@@ -740,11 +745,13 @@ def run_ours(args, w):
     flop = plan.flop
     ws = plan.workspace()
     cap = None
+    count_only = bool(w.get("count_only"))
+    cnt_dev = torch.zeros(1, dtype=torch.int64, device="cuda")
     if w.get("exact"):  # size C by a counting run (a flop-sized C would not fit)
         cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
         binding.numeric_count(plan, Ad, Bd, ws, cnt)
         cap = int(cnt.item())
-    C = binding.alloc_output(plan, rowptr64=True, cap=cap)
+    C = None if count_only else binding.alloc_output(plan, rowptr64=True, cap=cap)
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
     binding.set_phase_events(handle, ev)
 
@@ -754,7 +761,10 @@ def run_ours(args, w):
         p = binding.symbolic(Ad, Bd, dtype=dt, config=cfg, handle=handle)
         if record is not None:
             record[1].record(stream)
-        binding.numeric(p, Ad, Bd, C, ws)
+        if count_only:
+            binding.numeric_count(p, Ad, Bd, ws, cnt_dev)
+        else:
+            binding.numeric(p, Ad, Bd, C, ws)
         if record is not None:
             record[2].record(stream)
         return p
@@ -764,7 +774,7 @@ def run_ours(args, w):
         p = step()
     if p.status() != 0:
         raise RuntimeError("device-side error during warm-up")
-    nnz_c = int(C.rowptr[-1].item())
+    nnz_c = int(cnt_dev.item()) if count_only else int(C.rowptr[-1].item())
 
     sampler = ClockSampler(torch.cuda.current_device())
     sampler.start()
@@ -803,15 +813,16 @@ def run_ours(args, w):
     by = model.bytes_alg(A.nrows, A.ncols, A.nnz, B.nnz, flop, nnz_c, val_in=8, tuple_bytes=tuple_bytes,
                          val_out=8, rowptr_out=8)
     hbm, peak_kind = measured_peaks()
+    c_write = by.compress if count_only else 0  # a counting run writes no entry of C
     kern = {"expand": (by.expand, phase_ms["expand"] / args.steps, "k_expand", "pb_expand.cu"),
-            "sort_compress": (by.sort + by.compress, phase_ms["sort_compress"] / args.steps, "k_binsort",
+            "sort_compress": (by.sort + by.compress - c_write, phase_ms["sort_compress"] / args.steps, "k_binsort",
                               "pb_binsort.cu")}
     dom = max(kern, key=lambda k: kern[k][1])
     bytes_dom, ms_dom, kname, _ = kern[dom]
     achieved = bytes_dom / (ms_dom / 1e3) / 1e9
     numeric_ms = (phase_ms["reset"] + phase_ms["expand"] + phase_ms["sort_compress"]) / args.steps
-    pct_numeric = by.numeric / (numeric_ms / 1e3) / 1e9 / hbm
-    pct_step = by.total / (ms_per_step / 1e3) / 1e9 / hbm
+    pct_numeric = (by.numeric - c_write) / (numeric_ms / 1e3) / 1e9 / hbm
+    pct_step = (by.total - c_write) / (ms_per_step / 1e3) / 1e9 / hbm
 
     line = {
         "metric": METRIC, "value": value, "unit": "GFLOPS", "n_gpus": world, "steps": args.steps,
@@ -820,6 +831,7 @@ def run_ours(args, w):
         "config": {"workload": w["desc"], "n": A.nrows, "nnz_a": A.nnz, "flop": flop, "nnz_c": nnz_c,
                    "npanels": plan.npanels, "tuple_bytes": tuple_bytes, "deterministic": args.deterministic,
                    "cf": flop / max(nnz_c, 1), "nbins": plan.nbins, "bin_capacity": args.capacity or 4096,
+                   "counting_run": count_only,
                    "l2": "no flush: the inputs and the tuple buffer each exceed the 129 MB L2",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": hbm, "unit": "GB/s",
@@ -840,9 +852,13 @@ def run_ours(args, w):
         "clocks": clocks,
     }
 
-    if dt == binding.PB_F64_F32TUPLE and rank == 0:
+    if dt == binding.PB_F64_F32TUPLE and rank == 0 and not count_only:
         line["accuracy"] = f32_tuple_accuracy(A, B, C, nnz_c)
-    if not args.no_e2e and not w.get("exact"):
+    if args.compare_f32_tuples and rank == 0 and world == 1 and args.workload == "er21":
+        del C, ws, plan
+        torch.cuda.empty_cache()
+        line["fp32_tuples_vs_fp64"] = compare_tuple_forms(args, torch, binding)
+    if not args.no_e2e and not w.get("exact") and not count_only:
         line["e2e"] = run_e2e(args, A, B, handle, torch, binding, flop)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
@@ -860,6 +876,40 @@ def run_ours(args, w):
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def compare_tuple_forms(args, torch, binding):
+    """The mixed-precision configuration (ER n=2^22, d=8): numeric phase with FP64
+    tuples and with FP32 tuples merged in FP64, same inputs, same launch sequence
+    (CUDA events; median of the steps)."""
+    import synth
+    A, B = synth.er(1 << 22, 8, seed=4)
+    Ad, Bd = binding.csc_to_device(A), binding.csr_to_device(B)
+    handle = binding.Handle()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    binding.set_phase_events(handle, ev)
+    out = {"workload": "ER C=A*A, n=2^22, d=8, FP64 values", "steps": 5}
+    for name, dt in (("fp64", binding.PB_F64), ("fp32_tuples", binding.PB_F64_F32TUPLE)):
+        plan = binding.symbolic(Ad, Bd, dtype=dt, handle=handle)
+        ws = plan.workspace()
+        C = binding.alloc_output(plan, rowptr64=True)
+        for _ in range(3):
+            binding.numeric(plan, Ad, Bd, C, ws)
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(5):
+            binding.numeric(plan, Ad, Bd, C, ws)
+            ev[3].synchronize()
+            ms.append(ev[0].elapsed_time(ev[3]))
+        if plan.status() != 0:
+            raise RuntimeError(f"device status {plan.status()} in the {name} comparison")
+        t = statistics.median(ms)
+        out[name] = {"numeric_ms": t, "gflops_numeric": 2.0 * plan.flop / (t / 1e3) / 1e9}
+        del C, ws, plan
+        torch.cuda.empty_cache()
+    out["fp32_tuples_speedup"] = out["fp64"]["numeric_ms"] / out["fp32_tuples"]["numeric_ms"]
+    binding.set_phase_events(handle, None)
+    return out
 
 
 def f32_tuple_accuracy(A, B, C, nnz_c, budget_s: float = 3.0):
@@ -929,6 +979,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="batch workload: skip the autotuner")
+    ap.add_argument("--no-compare", dest="compare_f32_tuples", action="store_false",
+                    help="default workload: skip the FP32-tuple vs FP64 comparison at ER n=2^22")
     ap.add_argument("--deterministic", action="store_true",
                     help="single products: fixed tuple positions, bitwise-reproducible values")
     args = ap.parse_args()
