@@ -278,9 +278,12 @@ int64_t pb_kernel_launches(void);
  *               order after the last kernel, PB_OK or the device-detected
  *               error of the batch: PB_ERR_OVERFLOW (a C[i] too small),
  *               PB_ERR_WORKSPACE (tuples do not fit), PB_ERR_UNSUPPORTED (a
- *               single row of some product has more tuples than that
- *               product's bin capacity: run it with pb_spgemm_numeric),
+ *               row above its product's bin capacity in a product with
+ *               B.ncols > 2^22: run it with pb_spgemm_numeric),
  *               PB_ERR_TIMEOUT.
+ * Rows above their product's bin capacity (hub rows, Sec. III-D) are found on
+ * the device and merged in dense column tiles inside the batch (products with
+ * B.ncols <= 2^22); the workspace the query reports covers their scratch.
  * Limits: count <= 2^20; the sums over the batch of A.nrows, A.ncols and
  * nnz(A) each below 2^31.
  * Errors (returned): INVALID_ARG, SHAPE, UNSUPPORTED_DTYPE, UNSUPPORTED, CUDA.
@@ -296,8 +299,9 @@ typedef struct pb_batch_tune {
 
 /* Workspace for pb_spgemm_batch on these operands and, per product (host
  * arrays of count entries, either may be NULL), its flop (Alg. 3; a C
- * capacity that always suffices) and its largest per-row flop (a product
- * whose largest row exceeds its bin capacity is rejected by the batch).
+ * capacity that always suffices) and its largest per-row flop.  The workspace
+ * holds the scratch of every row above 2048 tuples, so it suffices for any
+ * bin capacity the tuning table may choose.
  * Synchronises `stream` once; allocates a temporary buffer through the
  * handle's allocator. */
 pb_status pb_spgemm_batch_query(pb_handle *h, int32_t count, const pb_csc *A, const pb_csr *B, pb_dtype dtype,

@@ -12,6 +12,13 @@
 // product's first bin, so prefixes (= C offsets) are product-local and every
 // bin writes straight into its own product's C.
 //
+// Rows above their product's bin capacity (hub rows, Sec. III-D) are listed on
+// the device while the bins are cut, merged in dense column tiles after the
+// expand (the single-product oversize kernels, reading the list's size from
+// the device), published in their product's look-back chain by the sort and
+// copied into C after it.  Their scratch follows the bins' tuples in the same
+// buffer.
+//
 // Everything the kernels need is computed on the device: the host only packs
 // the products' pointers and sizes into launch parameters, so a call makes no
 // host-device copy and no host synchronisation and can be captured into a
@@ -60,7 +67,7 @@ struct LevelRows {
 // Device arrays of one batch, carved from the caller's workspace.
 struct BatchWs {
     BatchHeader *bhdr;
-    uint32_t *err, *tickets, *n_long;
+    uint32_t *err, *tickets, *n_long, *n_over, *row_ticket;
     BatchDesc *desc;
     BatchProd *prod;
     int32_t *tiles_m, *tiles_k, *tiles_e;
@@ -77,6 +84,15 @@ struct BatchWs {
     uint32_t *keys;
     void *vals;
     int64_t chunk_cap, tuple_cap;
+    // rows above the bin capacity (oversize bins)
+    int64_t *over_scan;   // [M+2] index in the oversize list of an oversize bin
+    int64_t *over_count;  // [3] oversize bins, their work items (both 0 unless everything fits),
+                          // offset of the work items' histograms in `keys`
+    uint32_t *order_cnt;  // [128]
+    int64_t *over_bin, *over_chunk_off, *over_tuple_off, *over_u, *over_p;  // [n_over_cap (+1)]
+    int32_t *row_order;       // [n_over_cap]
+    int32_t *over_chunk_bin;  // [ochunk_cap]
+    int64_t n_over_cap, ochunk_cap;
 };
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
@@ -100,7 +116,9 @@ size_t carve_fixed(BatchWs &w, char *base, int32_t count, int64_t M, int64_t K, 
     uint32_t *ctrl = c.take<uint32_t>(256);
     w.err = ctrl;
     w.n_long = ctrl ? ctrl + 1 : nullptr;
-    w.tickets = ctrl ? ctrl + 8 : nullptr;
+    w.tickets = ctrl ? ctrl + 8 : nullptr;     // one per capacity level
+    w.row_ticket = ctrl ? ctrl + 16 : nullptr;  // [2] oversize rows taken by the dense and copy kernels
+    w.n_over = ctrl ? ctrl + 20 : nullptr;      // words 32.. hold the expand's work counter
     w.desc = c.take<BatchDesc>(sizeof(BatchDesc) * (size_t)count);
     w.prod = c.take<BatchProd>(sizeof(BatchProd) * (size_t)count);
     w.tiles_m = c.take<int32_t>(4 * ((size_t)count + 1));
@@ -119,6 +137,9 @@ size_t carve_fixed(BatchWs &w, char *base, int32_t count, int64_t M, int64_t K, 
     w.bin_off = c.take<int64_t>(8 * ((size_t)M + 2));
     w.cursor = c.take<uint64_t>(8 * ((size_t)M + 1));
     w.status = c.take<uint64_t>(8 * ((size_t)M + 1));
+    w.over_scan = c.take<int64_t>(8 * ((size_t)M + 2));
+    w.over_count = c.take<int64_t>(24);
+    w.order_cnt = c.take<uint32_t>(512);
     const int64_t scan_n = std::max<int64_t>(std::max<int64_t>(M, K), 1);
     w.scan_tmp = c.take<int64_t>(8 * (size_t)scan_tmp_elems(scan_n));
     return align256(c.off);
@@ -126,11 +147,22 @@ size_t carve_fixed(BatchWs &w, char *base, int32_t count, int64_t M, int64_t K, 
 
 constexpr size_t kSlack = 1024;
 
-// Bytes of the work-item table and tuples for `tuples` slots.
+// Oversize rows hold more than BATCH_MIN_CAPACITY tuples each, so `tuples`
+// slots bound their number, and their OVER_CHUNK-tuple work items (a row of
+// N > OVER_CHUNK / 2 tuples has ceil(N / OVER_CHUNK) < 2N / OVER_CHUNK).
+int64_t n_over_cap_of(int64_t tuples) { return tuples / BATCH_MIN_CAPACITY + 1; }
+int64_t ochunk_cap_of(int64_t tuples) { return tuples / (OVER_CHUNK / 2) + 1; }
+
+size_t over_bytes(int64_t tuples) {
+    const size_t no = (size_t)n_over_cap_of(tuples), oc = (size_t)ochunk_cap_of(tuples);
+    return 5 * align256(8 * (no + 1)) + align256(4 * no) + align256(4 * oc);
+}
+
+// Bytes of the work-item table, the tuples and the oversize-row arrays for `tuples` slots.
 size_t tail_bytes(int64_t tuples, int32_t count, size_t tb) {
     const int64_t chunks = tuples / MIN_CHUNK + count + 2;
     return align256(4 * ((size_t)chunks + 1)) + align256(4 * (size_t)chunks) + align256(4 * (size_t)tuples) +
-           align256(tb * (size_t)tuples) + kSlack;
+           align256(tb * (size_t)tuples) + over_bytes(tuples) + kSlack;
 }
 
 // Carve the work-item table and the tuples from what the workspace has left.
@@ -139,8 +171,12 @@ void carve_tail(BatchWs &w, char *base, size_t fixed, size_t ws_bytes, int32_t c
     w.tuple_cap = 0;
     if (ws_bytes <= fixed + kSlack + 8 * ((size_t)count + 4)) return;
     const size_t rem = ws_bytes - fixed - kSlack - 8 * ((size_t)count + 4);
-    // per tuple slot: 4 key bytes, tb value bytes, 8/MIN_CHUNK bytes of work-item table
-    int64_t tuples = (int64_t)((rem * MIN_CHUNK) / ((4 + tb) * MIN_CHUNK + 8));
+    // per tuple slot: 4 key bytes, tb value bytes, 8/MIN_CHUNK bytes of work-item
+    // table and the oversize-row arrays (44 bytes per BATCH_MIN_CAPACITY slots,
+    // 4 per OVER_CHUNK / 2); each array rounds up to 256 bytes
+    const double per = 4.0 + (double)tb + 8.0 / MIN_CHUNK + 44.0 / BATCH_MIN_CAPACITY + 8.0 / OVER_CHUNK;
+    const double usable = (double)rem - 16.0 * 256.0 - 3000.0;
+    int64_t tuples = usable > 0 ? (int64_t)(usable / per) : 0;
     tuples &= ~int64_t(3);
     while (tuples > 0 && fixed + tail_bytes(tuples, count, tb) > ws_bytes) tuples -= 4;
     if (tuples <= 0) return;
@@ -151,8 +187,18 @@ void carve_tail(BatchWs &w, char *base, size_t fixed, size_t ws_bytes, int32_t c
     w.chunk_prod = c.take<int32_t>(4 * (size_t)chunks);
     w.keys = c.take<uint32_t>(4 * (size_t)tuples);
     w.vals = c.take<char>(tb * (size_t)tuples);
+    const size_t no = (size_t)n_over_cap_of(tuples), oc = (size_t)ochunk_cap_of(tuples);
+    w.over_bin = c.take<int64_t>(8 * (no + 1));
+    w.over_chunk_off = c.take<int64_t>(8 * (no + 1));
+    w.over_tuple_off = c.take<int64_t>(8 * (no + 1));
+    w.over_u = c.take<int64_t>(8 * (no + 1));
+    w.over_p = c.take<int64_t>(8 * (no + 1));
+    w.row_order = c.take<int32_t>(4 * no);
+    w.over_chunk_bin = c.take<int32_t>(4 * oc);
     w.chunk_cap = chunks;
     w.tuple_cap = tuples;
+    w.n_over_cap = (int64_t)no;
+    w.ochunk_cap = (int64_t)oc;
 }
 
 // ---------------------------------------------------------------------------
@@ -193,7 +239,7 @@ __global__ void k_bdesc(const DescBlock blk, BatchDesc *desc, BatchProd *prod, i
     if (i < blk.n) {
         const int q = blk.first + i;
         desc[q] = blk.d[i];
-        prod[q] = BatchProd{0, 0, 0, -1, 0};
+        prod[q] = BatchProd{0, 0, 0, -1, 0, 0};
         tiles_m[q] = blk.tiles[i][0];
         tiles_k[q] = blk.tiles[i][1];
         tiles_e[q] = blk.tiles[i][2];
@@ -307,12 +353,15 @@ __global__ void __launch_bounds__(T) k_brow_flop(int32_t count, const BatchDesc 
     }
 }
 
-// Largest light row (r <= capacity / 2) and largest row of each product; a row
-// above the product's bin capacity cannot be sorted on chip: the batch stops.
+// Largest light row (r <= capacity / 2) and largest row of each product, and
+// the oversize-row tuples at the smallest capacity (the workspace query's
+// bound).  A row above the product's bin capacity is merged in dense tiles; a
+// product whose columns are too wide for them cannot have one: the batch stops.
 __global__ void __launch_bounds__(T) k_bmax(int32_t count, const BatchDesc *__restrict__ desc,
                                             const int32_t *__restrict__ tiles_m, const int64_t *__restrict__ R,
                                             BatchProd *prod, uint32_t *err) {
     __shared__ unsigned long long sh[32];
+    __shared__ int64_t scratch[40];
     const int64_t ntiles = tiles_m[count];
     for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const int q = find_prod(tiles_m, count, t);
@@ -320,6 +369,7 @@ __global__ void __launch_bounds__(T) k_bmax(int32_t count, const BatchDesc *__re
         const int64_t lo = (t - tiles_m[q]) * (int64_t)BATCH_TILE;
         const int64_t heavy = d.capacity / 2;
         unsigned long long light = 0, top = 0;
+        int64_t ob = 0;
         for (int j = threadIdx.x; j < BATCH_TILE; j += T) {
             const int64_t i = lo + j;
             if (i < d.m) {
@@ -327,14 +377,18 @@ __global__ void __launch_bounds__(T) k_bmax(int32_t count, const BatchDesc *__re
                 const unsigned long long r = (unsigned long long)(R[g + 1] - R[g]);
                 if ((int64_t)r <= heavy && r > light) light = r;
                 if (r > top) top = r;
+                if (r > (unsigned long long)BATCH_MIN_CAPACITY)  // scratch tuples and digit histograms
+                    ob += (int64_t)((r + 3) & ~3ull) + 256 * (int64_t)ceil_div<unsigned long long>(r, OVER_CHUNK);
             }
         }
         light = block_max_u64(light, sh);
         top = block_max_u64(top, sh);
+        ob = block_reduce_sum<int64_t, T>(ob, scratch);
         if (threadIdx.x == 0) {
             if (light) atomicMax(&prod[q].max_light, light);
             if (top) atomicMax(&prod[q].max_row, top);
-            if ((int64_t)top > d.capacity) atomicOr(err, DEV_ERR_HEAVY_ROW);
+            if (ob) atomicAdd(reinterpret_cast<unsigned long long *>(&prod[q].over_bound), (unsigned long long)ob);
+            if ((int64_t)top > d.capacity && !d.over_ok) atomicOr(err, DEV_ERR_HEAVY_ROW);
         }
     }
 }
@@ -366,11 +420,14 @@ __global__ void __launch_bounds__(T) k_bflags(int32_t count, const BatchDesc *__
     }
 }
 
-// flags holds the exclusive scan of the bin starts (flags[M] = bins).
+// flags holds the exclusive scan of the bin starts (flags[M] = bins).  A bin
+// whose single row is above the product's capacity joins the oversize list.
 __global__ void __launch_bounds__(T) k_bbin_rows(int32_t count, const BatchDesc *__restrict__ desc,
                                                  const int32_t *__restrict__ tiles_m, const int64_t *__restrict__ flags,
-                                                 int32_t M, int32_t *bin_row, int32_t *bin_prod, BatchProd *prod,
-                                                 BatchHeader *bh, LevelRows lv) {
+                                                 const int64_t *__restrict__ R, int32_t M, int32_t *bin_row,
+                                                 int32_t *bin_prod, BatchProd *prod, BatchHeader *bh, LevelRows lv,
+                                                 int64_t *over_scan, int64_t *over_bin, uint32_t *n_over,
+                                                 int64_t n_over_cap, uint32_t *err) {
     const int64_t ntiles = tiles_m[count];
     for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const int q = find_prod(tiles_m, count, t);
@@ -385,6 +442,16 @@ __global__ void __launch_bounds__(T) k_bbin_rows(int32_t count, const BatchDesc 
                 bin_row[f] = (int32_t)g;
                 bin_prod[f] = q;
                 if (i == 0) prod[q].first_bin = f;
+                // a row above capacity / 2 is a bin of its own (k_bflags)
+                if (R[g + 1] - R[g] > d.capacity) {
+                    const uint32_t o = atomicAdd(n_over, 1u);
+                    if (o < n_over_cap) {
+                        over_bin[o] = f;
+                        over_scan[f] = o;
+                    } else {
+                        atomicOr(err, DEV_ERR_WORKSPACE);
+                    }
+                }
             }
         }
     }
@@ -437,6 +504,57 @@ __global__ void k_bbin_off(const int64_t *__restrict__ R, const int32_t *__restr
         bh->tuples = tot;
         if (tot > tuple_cap) atomicOr(err, DEV_ERR_WORKSPACE);
     }
+}
+
+// The oversize list's work items and scratch (one CTA): per oversize bin its
+// first OVER_CHUNK-tuple work item and its scratch offset.  The scratch follows
+// the bins' tuples in the tuple buffer and the work items' 256-entry digit
+// histograms follow the scratch (in the key array); then the work item -> bin
+// map.  The counts stay 0 (no oversize kernel does any work) unless
+// everything fits.
+__global__ void __launch_bounds__(1024) k_bover(const int64_t *__restrict__ R, const int32_t *__restrict__ bin_row,
+                                                const int64_t *__restrict__ over_bin, const uint32_t *n_over,
+                                                int64_t n_over_cap, int64_t ochunk_cap, int64_t tuple_cap,
+                                                const BatchHeader *bh, uint32_t *err, int64_t *over_chunk_off,
+                                                int64_t *over_tuple_off, int32_t *over_chunk_bin,
+                                                int64_t *over_count) {
+    __shared__ int64_t scratch[40];
+    __shared__ int32_t fits;
+    const int tid = threadIdx.x;
+    const int64_t n = (*err & DEV_ERR_BATCH_FATAL) ? 0 : min((int64_t)*n_over, n_over_cap);
+    const int64_t base = (bh->tuples + 3) & ~int64_t(3);
+    int64_t cc = 0, tc = 0;
+    for (int64_t o0 = 0; o0 < n; o0 += 1024) {
+        const int64_t o = o0 + tid;
+        int64_t N = 0;
+        if (o < n) {
+            const int64_t b = over_bin[o];
+            N = R[bin_row[b + 1]] - R[bin_row[b]];
+        }
+        int64_t tch, ttu;
+        const int64_t pc = block_exclusive_scan<int64_t, 1024>(ceil_div<int64_t>(N, OVER_CHUNK), scratch, &tch);
+        const int64_t pt = block_exclusive_scan<int64_t, 1024>((N + 3) & ~int64_t(3), scratch, &ttu);
+        if (o < n) {
+            over_chunk_off[o] = cc + pc;
+            over_tuple_off[o] = base + tc + pt;
+        }
+        cc += tch;
+        tc += ttu;
+    }
+    if (tid == 0) {
+        const bool ok = base + tc + 256 * cc <= tuple_cap && cc <= ochunk_cap;
+        if (!ok) atomicOr(err, DEV_ERR_WORKSPACE);
+        over_chunk_off[n] = cc;
+        over_tuple_off[n] = base + tc;
+        over_count[0] = ok ? n : 0;
+        over_count[1] = ok ? cc : 0;
+        over_count[2] = base + tc;
+        fits = ok ? 1 : 0;
+    }
+    __syncthreads();
+    if (!fits) return;
+    for (int64_t o = tid; o < n; o += 1024)
+        for (int64_t c = over_chunk_off[o]; c < over_chunk_off[o + 1]; ++c) over_chunk_bin[c] = (int32_t)o;
 }
 
 // Per A entry: its row's bin info, and the expand work items.  In product q
@@ -532,6 +650,8 @@ struct BatchHost {
     int64_t M = 0, K = 0, E = 0;
     LevelRows lv{};
     int64_t level_rows[NLEVELS] = {0, 0, 0};
+    bool any_over = false;  // some product may have rows above its capacity
+    int over_shift = 0;     // dense tiles: the partition digit is column >> over_shift
 };
 
 pb_status prepare(pb_handle *h, int32_t count, const pb_csc *A, const pb_csr *B, const pb_csr_out *C, pb_dtype dtype,
@@ -598,6 +718,11 @@ pb_status prepare(pb_handle *h, int32_t count, const pb_csc *A, const pb_csr *B,
         d.capacity = tune[i].bin_capacity;
         d.chunk = tune[i].expand_chunk;
         d.level = level[i];
+        d.over_ok = d.colbits <= 8 + OVER_DENSE_MAX_SHIFT ? 1 : 0;
+        if (d.over_ok) {
+            bh.any_over = true;
+            bh.over_shift = std::max(bh.over_shift, d.colbits - 8);
+        }
         bh.tiles[3 * (size_t)g + 0] = (int32_t)tm;
         bh.tiles[3 * (size_t)g + 1] = (int32_t)tk;
         bh.tiles[3 * (size_t)g + 2] = (int32_t)te;
@@ -673,13 +798,19 @@ pb_status launch_batch(pb_handle *h, const BatchHost &bh, const BatchWs &w, pb_d
         k_bflags<<<grid_cap(bh.tiles_total[0], 1, cap), T, 0, s>>>(count, w.desc, w.tiles_m, w.R, w.prod, w.flags);
         count_launches(2);
         PB_CUDA_H(h, scan_i64(w.flags, bh.M, w.scan_tmp, s));
-        k_bbin_rows<<<grid_cap(bh.tiles_total[0], 1, cap), T, 0, s>>>(count, w.desc, w.tiles_m, w.flags,
-                                                                      (int32_t)bh.M, w.bin_row, w.bin_prod, w.prod,
-                                                                      w.bhdr, bh.lv);
+        k_bbin_rows<<<grid_cap(bh.tiles_total[0], 1, cap), T, 0, s>>>(
+            count, w.desc, w.tiles_m, w.flags, w.R, (int32_t)bh.M, w.bin_row, w.bin_prod, w.prod, w.bhdr, bh.lv,
+            w.over_scan, w.over_bin, w.n_over, w.n_over_cap, w.err);
         k_browinfo<<<grid_cap(bh.tiles_total[0], 1, cap), T, 0, s>>>(count, w.desc, w.tiles_m, w.flags, w.bin_row,
                                                                      w.rowinfo);
         k_bbin_off<<<grid_cap(bh.M, T, 4096), T, 0, s>>>(w.R, w.bin_row, (int32_t)bh.M, w.bhdr, w.tuple_cap,
                                                          w.bin_off, w.cursor, w.status, w.err);
+        if (bh.any_over) {
+            k_bover<<<1, 1024, 0, s>>>(w.R, w.bin_row, w.over_bin, w.n_over, w.n_over_cap, w.ochunk_cap,
+                                       w.tuple_cap, w.bhdr, w.err, w.over_chunk_off, w.over_tuple_off,
+                                       w.over_chunk_bin, w.over_count);
+            count_launches(1);
+        }
         // 5. per A entry: bin info and expand work items
         k_bentry<<<grid_cap(bh.tiles_total[2], 1, cap), T, 0, s>>>(count, w.desc, w.tiles_e, w.acol, w.rowinfo,
                                                                    w.F, w.prod, w.err, w.ainfo, w.aspan, w.chunk_e,
@@ -713,8 +844,45 @@ pb_status launch_batch(pb_handle *h, const BatchHost &bh, const BatchWs &w, pb_d
         a.prod = w.prod;
         a.bhdr = w.bhdr;
         a.work = w.err + 32;  // the control block is zeroed at the start of the call
+        a.over_scan = w.over_scan;
+        a.over_u = w.over_u;
+        a.over_p = w.over_p;
+        a.over_passes = 1;
+        a.over_dense = 1;
+        OversizeArgs o{};
+        o.R = w.R;
+        o.bin_row = w.bin_row;
+        o.bin_off = w.bin_off;
+        o.over_bin = w.over_bin;
+        o.over_chunk_off = w.over_chunk_off;
+        o.over_tuple_off = w.over_tuple_off;
+        o.over_chunk_bin = w.over_chunk_bin;
+        o.n_over = w.n_over_cap;
+        o.over_chunks = w.ochunk_cap;
+        o.keys = w.keys;
+        o.vals = w.vals;
+        o.skeys = w.keys;  // the scratch follows the bins' tuples (k_bover)
+        o.svals = w.vals;
+        o.hist = nullptr;  // in the tuple buffer (dev_count[2])
+        o.over_u = w.over_u;
+        o.o_lo = 0;
+        o.o_hi = w.n_over_cap;
+        o.c_lo = 0;
+        o.c_hi = w.ochunk_cap;
+        o.dense = 1;
+        o.dense_shift = bh.over_shift;
+        o.wide = dtype == PB_F64_F32TUPLE ? 1 : 0;
+        o.row_ticket = w.row_ticket;
+        o.row_order = w.row_order;
+        o.order_cnt = w.order_cnt;
+        o.over_p = w.over_p;
+        o.dev_count = w.over_count;
+        o.desc = w.desc;
+        o.bin_prod = w.bin_prod;
         if (h->phase_on) PB_CUDA_H(h, cudaEventRecord(h->phase_ev[1], s));
         PB_CUDA_H(h, launch_expand_batch(a, s));
+        // rows above their capacity: one partition pass and dense tiles, before the sort publishes them
+        if (bh.any_over) PB_CUDA_H(h, launch_oversize(o, 1, dtype, h->num_sms, s));
         if (h->phase_on) PB_CUDA_H(h, cudaEventRecord(h->phase_ev[2], s));
         for (int l = 0; l < NLEVELS; ++l) {
             if (bh.level_rows[l] == 0) continue;
@@ -725,6 +893,7 @@ pb_status launch_batch(pb_handle *h, const BatchHost &bh, const BatchWs &w, pb_d
             a.bin_hi = bh.level_rows[l];  // bound on the level's bins: sizes the grid
             PB_CUDA_H(h, launch_binsort_batch(a, s));
         }
+        if (bh.any_over) PB_CUDA_H(h, launch_oversize_emit(o, dtype, h->num_sms, s));
         if (h->phase_on) PB_CUDA_H(h, cudaEventRecord(h->phase_ev[3], s));
     }
     k_bfinish<<<1, 1, 0, s>>>(w.err, device_status);
@@ -759,14 +928,16 @@ pb_status pb_spgemm_batch_query(pb_handle *h, int32_t count, const pb_csc *A, co
     h->free_fn(tmp, fixed, stream_, h->ctx);
     if (st != PB_OK) return st;
     if (e != cudaSuccess) return host_cuda_fail(h, e, "batch query");
-    int64_t total = 0;
+    int64_t total = 0, over = 0;
     for (int32_t g = 0; g < count; ++g) {
         const int32_t i = bh.order[g];
         total += prod[g].flop;
+        over += prod[g].over_bound;
         if (flop) flop[i] = prod[g].flop;
         if (max_row_flop) max_row_flop[i] = (int64_t)prod[g].max_row;
     }
-    const int64_t tuples = ((total + 3) & ~int64_t(3)) + 4 * bh.M + 8;
+    // the bins' tuples, then the scratch of the rows above capacity
+    const int64_t tuples = ((total + 3) & ~int64_t(3)) + 4 * bh.M + 8 + over;
     if (workspace_bytes) *workspace_bytes = fixed + tail_bytes(tuples, count, tuple_bytes(dtype));
     return PB_OK;
 }

@@ -742,6 +742,49 @@ __global__ void __launch_bounds__(THREADS, (THREADS <= 256 ? 4 : (THREADS <= 512
     }
 }
 
+// The product of batch bin b: where its merged entries go (thread 0).
+__device__ inline void load_bin_out(const NumericArgs &p, int64_t b, int64_t nbins, BinOut &o) {
+    const int32_t q = p.bin_prod[b];
+    const BatchDesc &d = p.desc[q];
+    o.rowptr64 = d.rowptr64;
+    o.rowptr32 = d.rowptr32;
+    o.colidx = d.colidxC;
+    o.valC = d.valC;
+    o.nnz_dev = d.nnz_dev;
+    o.cap = d.capC;
+    o.first = p.prod[q].first_bin;
+    o.rbase = d.mstart;
+    o.m = d.m;
+    o.colbits = d.colbits;
+    o.last = (b + 1 == nbins || p.bin_prod[b + 1] != q) ? 1 : 0;
+}
+
+// Batch bin b is one row above the capacity, merged in dense tiles before this
+// kernel (its merged count is known): publish the count in its product's
+// look-back chain, write the row pointer(s) and record the row's C offset for
+// the copy kernel that runs after the sort.
+template <int THREADS>
+__device__ void batch_oversize_bin(const NumericArgs &p, int64_t b, int32_t row0, int64_t nbins, BinOut &out,
+                                   int64_t *scratch, int32_t *marks) {
+    const int tid = threadIdx.x;
+    if (tid == 0) load_bin_out(p, b, nbins, out);
+    __syncthreads();
+    const int64_t o = p.over_scan[b];
+    const int64_t U = p.over_u[o];
+    const int64_t P = lookback_block<THREADS>(p.status, b, (uint64_t)U, p.err, scratch, marks, out.first);
+    if (tid == 0) {
+        const bool good = !(P + U > out.cap || (out.rowptr32 && P + U > 0x7fffffffll));
+        if (!good) atomicOr(p.err, DEV_ERR_OVERFLOW);
+        if (good) write_rowptr(out, row0 - out.rbase, P);
+        if (out.last) {
+            if (good) write_rowptr(out, out.m, P + U);
+            if (out.nnz_dev) *out.nnz_dev = P + U;
+        }
+        p.over_p[o] = good ? P : -1;
+    }
+    __syncthreads();  // the shared descriptor and look-back words are reused by the next bin
+}
+
 // BATCH: bins of the products of a batch that share one capacity level; each
 // bin writes into its own product's C (taken from the product's descriptor).
 template <int CAP, int THREADS, class TV, class OV, bool BATCH>
@@ -784,9 +827,8 @@ __global__ void __launch_bounds__(THREADS, (THREADS <= 256 ? 4 : (THREADS <= 512
         int64_t Nfull = p.R[row1] - p.R[row0];
         if (Nfull > CAP) {
             if constexpr (BATCH) {
-                // the symbolic phase never cuts such a bin for a batch; record it and skip the tuples
-                if (tid == 0) atomicOr(p.err, DEV_ERR_CAPACITY);
-                Nfull = 0;
+                batch_oversize_bin<THREADS>(p, b, row0, nbins, sm.out, sm.scratch, sm.marks);
+                continue;
             } else {
                 stream_oversize_bin<THREADS, TV, OV>(p, b, row0, row1, off, Nfull, colmask, sm.scratch,
                                                      &sm.prefix, &sm.ok);
@@ -804,22 +846,7 @@ __global__ void __launch_bounds__(THREADS, (THREADS <= 256 ? 4 : (THREADS <= 512
             bulk_g2s(sm.vin, gvals + off, n4 * (uint32_t)sizeof(TV), &sm.bar);
         }
         if constexpr (BATCH) {
-            if (tid == 0) {  // the bin's product, fetched while the copies are in flight
-                const int32_t q = p.bin_prod[b];
-                const BatchDesc &d = p.desc[q];
-                BinOut &o = sm.out;
-                o.rowptr64 = d.rowptr64;
-                o.rowptr32 = d.rowptr32;
-                o.colidx = d.colidxC;
-                o.valC = d.valC;
-                o.nnz_dev = d.nnz_dev;
-                o.cap = d.capC;
-                o.first = p.prod[q].first_bin;
-                o.rbase = d.mstart;
-                o.m = d.m;
-                o.colbits = d.colbits;
-                o.last = (b + 1 == nbins || p.bin_prod[b + 1] != q) ? 1 : 0;
-            }
+            if (tid == 0) load_bin_out(p, b, nbins, sm.out);  // fetched while the copies are in flight
         }
         for (int r = tid; r < rows_b; r += THREADS) sm.rowcnt[r] = 0;
         for (int i = tid; i <= CAP; i += THREADS) sm.cnt[i] = 0;

@@ -96,6 +96,8 @@ struct SymbolicArgs {
     int64_t *over_tuple_off;  // scratch offset of oversize bin o
 };
 
+struct BatchDesc;
+
 struct OversizeArgs {
     const int64_t *R;
     const int32_t *bin_row;
@@ -129,6 +131,14 @@ struct OversizeArgs {
     int64_t *over_p;    // [n_over] C offset of each oversize row (-1: not written)
     int32_t *colidxC;   // C, for the copy of the segments once the offsets are known
     void *valC;
+    // Batches find their oversize rows on the device: dev_count[0] oversize bins,
+    // dev_count[1] work items (o_lo = c_lo = 0; o_hi and c_hi are then upper
+    // bounds that only size the grids), dev_count[2] the offset in `keys` of
+    // the work items' histograms (hist is unused), and each row's C is its
+    // product's (desc[bin_prod[bin]]).  Null for a single product.
+    const int64_t *dev_count;
+    const BatchDesc *desc;
+    const int32_t *bin_prod;
 };
 
 template <class T>
@@ -286,6 +296,7 @@ constexpr int OVER_DENSE_MAX_SHIFT = 14;
 // straddle two products; tile_*[p] is the first tile of product p.
 // ---------------------------------------------------------------------------
 constexpr int BATCH_TILE = 1024;
+constexpr int BATCH_MIN_CAPACITY = 2048;  // smallest bin capacity a batched product can be tuned to
 
 struct BatchDesc {
     const int32_t *colptrA, *rowidxA;
@@ -301,6 +312,7 @@ struct BatchDesc {
     int32_t m, k, n, nnzA;
     int32_t mstart, kstart, estart;  // first global row, column and A entry
     int32_t colbits, rmax_log2, capacity, chunk, level;
+    int32_t over_ok;  // rows above the capacity may be merged in dense tiles (B.ncols <= 2^(8 + OVER_DENSE_MAX_SHIFT))
 };
 
 // Per-product values found on the device.
@@ -310,6 +322,7 @@ struct BatchProd {
     unsigned long long max_row;    // largest row flop
     int64_t first_bin;
     int64_t chunk_base;            // first expand work item
+    int64_t over_bound;            // sum of round_up(r, 4) over rows with r > BATCH_MIN_CAPACITY tuples
 };
 
 struct BatchHeader {

@@ -33,6 +33,15 @@ struct ChunkRef {
     int64_t o, bin, start, len;
 };
 
+// End of the oversize bins and of their work items: the launch's values, or
+// for a batch the counts its symbolic phase found on the device.
+__device__ inline int64_t over_o_hi(const OversizeArgs &a) { return a.dev_count ? a.dev_count[0] : a.o_hi; }
+__device__ inline int64_t over_c_hi(const OversizeArgs &a) { return a.dev_count ? a.dev_count[1] : a.c_hi; }
+// Per-work-item digit histograms: a batch keeps them in its tuple buffer.
+__device__ inline uint32_t *over_hist(const OversizeArgs &a) {
+    return a.dev_count ? a.keys + a.dev_count[2] : a.hist;
+}
+
 __device__ inline ChunkRef chunk_ref(const OversizeArgs &a, int64_t c) {
     ChunkRef r;
     r.o = a.over_chunk_bin[c];
@@ -60,7 +69,9 @@ __device__ inline void pass_buffers(const OversizeArgs &a, int pass, const Chunk
 template <class TV>
 __global__ void __launch_bounds__(OT) k_over_hist(const OversizeArgs a, int pass, int shift) {
     __shared__ uint32_t h[256];
-    for (int64_t c = a.c_lo + blockIdx.x; c < a.c_hi; c += gridDim.x) {
+    const int64_t c_hi = over_c_hi(a);
+    uint32_t *hist = over_hist(a);
+    for (int64_t c = a.c_lo + blockIdx.x; c < c_hi; c += gridDim.x) {
         const ChunkRef r = chunk_ref(a, c);
         const uint32_t *sk;
         const TV *sv;
@@ -71,7 +82,7 @@ __global__ void __launch_bounds__(OT) k_over_hist(const OversizeArgs a, int pass
         __syncthreads();
         for (int64_t q = threadIdx.x; q < r.len; q += OT) atomicAdd(&h[(sk[r.start + q] >> shift) & 255u], 1u);
         __syncthreads();
-        for (int i = threadIdx.x; i < 256; i += OT) a.hist[(c - a.c_lo) * 256 + i] = h[i];
+        for (int i = threadIdx.x; i < 256; i += OT) hist[(c - a.c_lo) * 256 + i] = h[i];
         __syncthreads();
     }
 }
@@ -81,17 +92,19 @@ __global__ void __launch_bounds__(OT) k_over_hist(const OversizeArgs a, int pass
 __global__ void __launch_bounds__(256) k_over_offsets(const OversizeArgs a) {
     __shared__ int64_t scratch[40];
     const int d = threadIdx.x;  // one digit value per thread
-    for (int64_t o = a.o_lo + blockIdx.x; o < a.o_hi; o += gridDim.x) {
+    const int64_t o_hi = over_o_hi(a);
+    uint32_t *hist = over_hist(a);
+    for (int64_t o = a.o_lo + blockIdx.x; o < o_hi; o += gridDim.x) {
         const int64_t c0 = a.over_chunk_off[o] - a.c_lo, c1 = a.over_chunk_off[o + 1] - a.c_lo;
         uint32_t run = 0;
         for (int64_t c = c0; c < c1; ++c) {
-            const uint32_t v = a.hist[c * 256 + d];
-            a.hist[c * 256 + d] = run;
+            const uint32_t v = hist[c * 256 + d];
+            hist[c * 256 + d] = run;
             run += v;
         }
         int64_t total;
         const int64_t base = block_exclusive_scan<int64_t, 256>((int64_t)run, scratch, &total);
-        for (int64_t c = c0; c < c1; ++c) a.hist[c * 256 + d] += (uint32_t)base;
+        for (int64_t c = c0; c < c1; ++c) hist[c * 256 + d] += (uint32_t)base;
         __syncthreads();
     }
 }
@@ -113,7 +126,9 @@ __global__ void __launch_bounds__(OT, 2) k_over_scatter(const OversizeArgs a, in
     extern __shared__ __align__(16) unsigned char smraw[];
     ScatterSmem<TV> &m = *reinterpret_cast<ScatterSmem<TV> *>(smraw);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int64_t c = a.c_lo + blockIdx.x; c < a.c_hi; c += gridDim.x) {
+    const int64_t c_hi = over_c_hi(a);
+    const uint32_t *hist = over_hist(a);
+    for (int64_t c = a.c_lo + blockIdx.x; c < c_hi; c += gridDim.x) {
         const ChunkRef r = chunk_ref(a, c);
         const uint32_t *sk;
         const TV *sv;
@@ -173,7 +188,7 @@ __global__ void __launch_bounds__(OT, 2) k_over_scatter(const OversizeArgs a, in
             for (int j = 0; j < 8; ++j) {
                 const int d = lane * 8 + j;
                 m.cbase[d] = pre;
-                m.gbase[d] = (int64_t)a.hist[(c - a.c_lo) * 256 + d] - pre;
+                m.gbase[d] = (int64_t)hist[(c - a.c_lo) * 256 + d] - pre;
                 pre += t[j];
             }
         }
@@ -202,7 +217,8 @@ __global__ void __launch_bounds__(OT, 2) k_over_scatter(const OversizeArgs a, in
 // Number of merged entries of each oversize bin = number of run heads.
 __global__ void __launch_bounds__(OT) k_over_heads(const OversizeArgs a, int passes) {
     __shared__ int64_t scratch[40];
-    for (int64_t c = a.c_lo + blockIdx.x; c < a.c_hi; c += gridDim.x) {
+    const int64_t c_hi = over_c_hi(a);
+    for (int64_t c = a.c_lo + blockIdx.x; c < c_hi; c += gridDim.x) {
         const ChunkRef r = chunk_ref(a, c);
         const uint32_t *k = (passes & 1) ? a.skeys + (a.over_tuple_off[r.o] - a.over_base)
                                          : a.keys + (a.bin_off[r.bin] - a.tuple_base);
@@ -229,7 +245,8 @@ __device__ inline int over_size_class(const OversizeArgs &a, int64_t o) {
 }
 
 __global__ void k_over_order_count(const OversizeArgs a) {
-    for (int64_t o = a.o_lo + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < a.o_hi;
+    const int64_t o_hi = over_o_hi(a);
+    for (int64_t o = a.o_lo + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < o_hi;
          o += (int64_t)gridDim.x * blockDim.x)
         atomicAdd(&a.order_cnt[over_size_class(a, o)], 1u);
 }
@@ -242,7 +259,8 @@ __global__ void k_over_order_place(const OversizeArgs a) {
         start[threadIdx.x] = s;
     }
     __syncthreads();
-    for (int64_t o = a.o_lo + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < a.o_hi;
+    const int64_t o_hi = over_o_hi(a);
+    for (int64_t o = a.o_lo + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < o_hi;
          o += (int64_t)gridDim.x * blockDim.x) {
         const int c = over_size_class(a, o);
         a.row_order[start[c] + atomicAdd(&a.order_cnt[64 + c], 1u)] = (int32_t)(o - a.o_lo);
@@ -288,20 +306,21 @@ __global__ void __launch_bounds__(DT) k_over_dense(const OversizeArgs a, int gro
         seen[i] = 0;
     }
     const int nslab = W / DT;  // W is a multiple of DT
+    const int64_t o_hi = over_o_hi(a);
     __shared__ int64_t next_row;
     while (true) {
         // rows are taken through a ticket, largest size class first
         if (tid == 0) {
             const int64_t t = (int64_t)atomicAdd(&a.row_ticket[0], 1u);
-            next_row = t < a.o_hi - a.o_lo ? a.o_lo + a.row_order[t] : a.o_hi;
+            next_row = t < o_hi - a.o_lo ? a.o_lo + a.row_order[t] : o_hi;
         }
         __syncthreads();
         const int64_t o = next_row;
-        if (o >= a.o_hi) break;
+        if (o >= o_hi) break;
         const int64_t bin = a.over_bin[o];
         const int64_t N = a.R[a.bin_row[bin + 1]] - a.R[a.bin_row[bin]];
         const int64_t c0 = a.over_chunk_off[o] - a.c_lo;  // the bin's first work item holds its digit offsets
-        offs[tid] = a.hist[c0 * 256 + tid];
+        offs[tid] = over_hist(a)[c0 * 256 + tid];
         if (tid == 0) offs[256] = N;
         __syncthreads();
         uint32_t *xk = a.skeys + (a.over_tuple_off[o] - a.over_base);
@@ -400,35 +419,42 @@ cudaError_t run_dense(const OversizeArgs &a, int num_sms, cudaStream_t s) {
 // scratch region) to C at the offset the sort kernel recorded; CTA per row.
 template <class TV, class OV, bool WIDE>
 __global__ void __launch_bounds__(256) k_over_emit(const OversizeArgs a) {
-    OV *valC = static_cast<OV *>(a.valC);
+    const int64_t o_hi = over_o_hi(a);
     __shared__ int64_t next_row;
     while (true) {
         if (threadIdx.x == 0) {
             const int64_t t = (int64_t)atomicAdd(&a.row_ticket[1], 1u);
-            next_row = t < a.o_hi - a.o_lo ? a.o_lo + a.row_order[t] : a.o_hi;
+            next_row = t < o_hi - a.o_lo ? a.o_lo + a.row_order[t] : o_hi;
         }
         __syncthreads();
         const int64_t o = next_row;
         __syncthreads();  // every thread has its row before the ticket word is reused
-        if (o >= a.o_hi) break;
+        if (o >= o_hi) break;
         const int64_t P = a.over_p[o];
         if (P < 0) continue;
         const int64_t U = a.over_u[o];
+        const int64_t bin = a.over_bin[o];
         const uint32_t *xk = a.skeys + (a.over_tuple_off[o] - a.over_base);
+        int32_t *colidxC = a.colidxC;
+        OV *valC = static_cast<OV *>(a.valC);
+        if (a.desc) {  // batch: the row's product's C
+            const BatchDesc &d = a.desc[a.bin_prod[bin]];
+            colidxC = d.colidxC;
+            valC = static_cast<OV *>(d.valC);
+        }
         if (WIDE) {
-            const int64_t bin = a.over_bin[o];
             const int64_t half = (a.R[a.bin_row[bin + 1]] - a.R[a.bin_row[bin]] + 1) / 2;
             const double *wa = reinterpret_cast<const double *>(a.keys + (a.bin_off[bin] - a.tuple_base));
             const double *wb =
                 reinterpret_cast<const double *>(static_cast<const TV *>(a.vals) + (a.bin_off[bin] - a.tuple_base));
             for (int64_t i = threadIdx.x; i < U; i += blockDim.x) {
-                a.colidxC[P + i] = (int32_t)xk[i];
+                colidxC[P + i] = (int32_t)xk[i];
                 valC[P + i] = (OV)(i < half ? wa[i] : wb[i - half]);
             }
         } else {
             const TV *xv = static_cast<const TV *>(a.svals) + (a.over_tuple_off[o] - a.over_base);
             for (int64_t i = threadIdx.x; i < U; i += blockDim.x) {
-                a.colidxC[P + i] = (int32_t)xk[i];
+                colidxC[P + i] = (int32_t)xk[i];
                 valC[P + i] = (OV)xv[i];
             }
         }

@@ -3,8 +3,9 @@
 Every product of a batch must match the oracle as if it were computed alone:
 structure bit-exact, values within 64 * eps * sum_k |a_ik b_kj|.  Batches mix
 sizes, densities, rectangular shapes, empty products and all three sort
-capacity levels; one test captures the batch into a CUDA graph and replays it
-after the operand values change.
+capacity levels, and rows above every capacity (R-MAT hub rows, dense rows);
+two tests capture a batch into a CUDA graph and replay it after the operand
+values change.
 """
 import numpy as np
 import pytest
@@ -51,7 +52,7 @@ def mixed_problems(seed=0):
     probs.append(synth.identity(777))
     P = synth.permutation(500, seed=3)
     probs.append((P[0], P[1]))
-    probs.append(synth.rmat(10, 4, seed=5))                 # skewed rows (below the bin capacity)
+    probs.append(synth.rmat(10, 4, seed=5))                 # skewed rows
     return probs
 
 
@@ -110,16 +111,13 @@ def all_classes(probs, cap, rmax=11, chunk=4096):
 
 @pytest.mark.parametrize("cap,rmax,chunk", [(2048, 11, 256), (8192, 4, 16384), (4096, 1, 1024)])
 def test_batch_one_level(pb, cap, rmax, chunk):
-    # a row above the bin capacity is rejected by the batch (tested below): leave such products out
-    probs = [(A, B) for A, B in mixed_problems(3)
-             if A.nrows == 0 or int(np.max(oracle.row_flop(A, B), initial=0)) <= cap]
+    probs = mixed_problems(3)
     check_all(run_batch(pb, probs, tuning=all_classes(probs, cap, rmax, chunk)), probs, EPS["f64"])
 
 
 def test_batch_three_levels_interleaved(pb):
     """Products of one batch spread over the 2048/4096/8192 sort launches."""
-    probs = [(A, B) for A, B in mixed_problems(4)
-             if A.nrows == 0 or int(np.max(oracle.row_flop(A, B), initial=0)) <= 2048]
+    probs = mixed_problems(4)
     table = all_classes(probs, 4096)
     caps = [2048, 4096, 8192]
     for j, e in enumerate(table):
@@ -215,23 +213,98 @@ def test_batch_c_overflow_status(pb):
     assert_matches(bt.result(0), oracle.spgemm(*probs[0]), EPS["f64"])
 
 
-def test_batch_heavy_row_rejected(pb):
-    """A row with more tuples than its bin capacity: reported by the query and by the device status."""
-    rng = np.random.default_rng(0)
+def hub_problems(seed=0):
+    """R-MAT products of scale 10..12, whose hub rows exceed every bin capacity,
+    mixed with ER products and with single dense rows at a product's first and
+    last row (one row of 100 x 100 = 10,000 tuples merging into 100 entries)."""
+    rng = np.random.default_rng(seed)
+    probs = [synth.rmat(sc, ef, seed=seed * 100 + i)
+             for i, (sc, ef) in enumerate([(10, 8), (11, 8), (12, 8), (12, 16), (10, 16), (11, 4)])]
+    probs += [synth.er(3000, 8, seed=seed + 7), synth.er(500, 3, seed=seed + 8)]
     k = 100
-    A = synth.coo_to_csc(3, k, np.zeros(k, np.int64), np.arange(k), rng.uniform(-1, 1, k))   # row 0 full
     Bd = rng.uniform(-1, 1, (k, 100))
     r, c = np.nonzero(Bd)
-    B = synth.coo_to_csr(k, 100, r, c, Bd[r, c])                                         # dense 100 x 100
-    probs = [synth.er(500, 3, seed=9), (A, B)]
+    B = synth.coo_to_csr(k, 100, r, c, Bd[r, c])
+    for row in (0, 2):
+        A = synth.coo_to_csc(3, k, np.full(k, row, np.int64), np.arange(k), rng.uniform(-1, 1, k))
+        probs.append((A, B))
+    return probs
+
+
+def test_batch_hub_rows(pb):
+    """Rows above the bin capacity are merged inside the batch (Sec. III-D)."""
+    probs = hub_problems(0)
+    heavy = [int(oracle.row_flop(A, B).max()) for A, B in probs]
+    assert max(heavy) > 8192 and sum(h > 4096 for h in heavy) >= 6
+    bt = run_batch(pb, probs)
+    for i, (A, B) in enumerate(probs):
+        assert int(bt.max_row[i]) == heavy[i]
+    check_all(bt, probs, EPS["f64"])
+
+
+@pytest.mark.parametrize("cap", [2048, 4096, 8192])
+def test_batch_hub_rows_each_level(pb, cap):
+    probs = hub_problems(1)
+    check_all(run_batch(pb, probs, tuning=all_classes(probs, cap)), probs, EPS["f64"])
+
+
+def test_batch_hub_rows_fp32_tuples_and_int32_rowptr(pb):
+    probs = hub_problems(2)
+    probs32 = [(synth.CSC(A.nrows, A.ncols, A.colptr, A.rowidx, A.val.astype(np.float32)),
+                synth.CSR(B.nrows, B.ncols, B.rowptr, B.colidx, B.val.astype(np.float32))) for A, B in probs]
+    check_all(run_batch(pb, probs32, dtype=1, vdt=torch.float32), probs32, EPS["f32"])
+    check_all(run_batch(pb, probs, dtype=2), probs, EPS["f32"])
+    check_all(run_batch(pb, probs, rowptr64=False), probs, EPS["f64"])
+
+
+def test_batch_hub_rows_cuda_graph_replay(pb):
+    """A batch with hub rows captured once and replayed after the values change."""
+    probs = hub_problems(3)
     handle = pb.Handle()
-    As = [pb.csc_to_device(a) for a, _ in probs]
-    Bs = [pb.csr_to_device(b) for _, b in probs]
+    As = [pb.csc_to_device(A) for A, _ in probs]
+    Bs = [pb.csr_to_device(B) for _, B in probs]
     bt = pb.Batch(As, Bs, handle=handle)
-    assert int(bt.max_row[1]) == 100 * 100
-    bt.run()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        bt.run(stream=s)
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    check_all(bt, probs, EPS["f64"])
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        bt.run(stream=s)
+    for rep in range(2):
+        rng = np.random.default_rng(200 + rep)
+        new = []
+        for (A, B), Ad, Bd in zip(probs, As, Bs):
+            av = rng.uniform(-1, 1, A.nnz)
+            bv = rng.uniform(-1, 1, B.nnz)
+            Ad.val.copy_(torch.from_numpy(av))
+            Bd.val.copy_(torch.from_numpy(bv))
+            new.append((synth.CSC(A.nrows, A.ncols, A.colptr, A.rowidx, av),
+                        synth.CSR(B.nrows, B.ncols, B.rowptr, B.colidx, bv)))
+        bt.device_status.fill_(-1)
+        torch.cuda.synchronize()
+        g.replay()
+        torch.cuda.synchronize()
+        check_all(bt, new, EPS["f64"])
+
+
+def test_batch_hub_row_in_too_wide_product_rejected(pb):
+    """A hub row of a product with more than 2^22 columns is beyond the dense tiles:
+    the batch reports PB_ERR_UNSUPPORTED and the single-product path computes it."""
+    rng = np.random.default_rng(0)
+    k, n = 100, (1 << 22) + 1
+    A = synth.coo_to_csc(3, k, np.zeros(k, np.int64), np.arange(k), rng.uniform(-1, 1, k))   # row 0 full
+    rows = np.repeat(np.arange(k), 50)
+    cols = np.concatenate([np.sort(rng.choice(n, 50, replace=False)) for _ in range(k)])
+    B = synth.coo_to_csr(k, n, rows, cols, rng.uniform(-1, 1, k * 50))                      # row flop 5000
+    probs = [synth.er(500, 3, seed=9), (A, B)]
+    bt = run_batch(pb, probs)
+    assert int(bt.max_row[1]) == 5000
     assert bt.status() == 9  # PB_ERR_UNSUPPORTED
-    C = pb.spgemm(As[1], Bs[1])   # the single-product path sorts such a row in global memory
+    C = pb.spgemm(pb.csc_to_device(A), pb.csr_to_device(B))
     assert_matches(C, oracle.spgemm(A, B), EPS["f64"])
 
 
