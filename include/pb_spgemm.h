@@ -211,10 +211,14 @@ pb_status pb_plan_export(const pb_plan *plan, int64_t *F, int64_t *R, int32_t *b
 /* Run only the expand phase into `workspace` (same layout numeric uses):
  * tuples of bin b occupy [bin_off[b], bin_off[b] + count_b) of the key array
  * that starts at workspace and the value array that starts at
- * workspace + pb_debug_values_offset(plan).  For tests of the expand step. */
+ * workspace + pb_debug_values_offset(plan).  When pb_debug_tuple_layout(plan)
+ * is 1 (4-byte values, no row above the bin capacity, not deterministic) tuple
+ * t is instead the pair of uint32 {key, value bits} at workspace + 8t.  For
+ * tests of the expand step. */
 pb_status pb_debug_expand(pb_handle *h, const pb_plan *plan, const pb_csc *A, const pb_csr *B,
                           void *workspace, size_t ws_bytes, pb_stream_t stream);
 size_t pb_debug_values_offset(const pb_plan *plan);
+int32_t pb_debug_tuple_layout(const pb_plan *plan);
 
 pb_status pb_plan_destroy(pb_plan *plan);
 

@@ -94,6 +94,7 @@ SIGNATURES = {
     "pb_plan_export": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP]),
     "pb_debug_expand": (ctypes.c_int, [_VP, _VP, ctypes.POINTER(_CSC), ctypes.POINTER(_CSR), _VP, _SZ, _VP]),
     "pb_debug_values_offset": (_SZ, [_VP]),
+    "pb_debug_tuple_layout": (ctypes.c_int32, [_VP]),
     "pb_plan_destroy": (ctypes.c_int, [_VP]),
     "pb_set_phase_events": (ctypes.c_int, [_VP, _VP]),
     "pb_kernel_launches": (_I64, []),
@@ -366,6 +367,11 @@ def debug_expand(plan: Plan, A: CscMatrix, B: CsrMatrix, workspace: torch.Tensor
     _check(h.lib, h.ptr, h.lib.pb_debug_expand(h.ptr, plan.ptr, ctypes.byref(cA), ctypes.byref(cB),
                                                workspace.data_ptr(), workspace.numel(), _stream_ptr(stream)))
     return workspace, int(h.lib.pb_debug_values_offset(plan.ptr))
+
+
+def debug_tuple_layout(plan: Plan) -> int:
+    """1 when the plan's tuples are packed {key, value bits} pairs of uint32, 0 for separate arrays."""
+    return int(plan.handle.lib.pb_debug_tuple_layout(plan.ptr))
 
 
 def spgemm_noalloc(A: CscMatrix, B: CsrMatrix, C: CsrMatrix, dtype: int = PB_F64,

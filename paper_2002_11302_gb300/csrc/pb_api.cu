@@ -55,6 +55,9 @@ struct pb_plan {
     int32_t *over_chunk_bin = nullptr;
     int over_passes = 0;
     int over_dense = 0, over_shift = 0;  // oversize rows merged in dense column tiles
+    // 4-byte values without oversize bins or fixed run positions: tuples are
+    // packed {key, value bits} pairs over the key and value regions
+    int packed = 0;
     // workspace layout of the numeric phase
     size_t ws_keys = 0, ws_vals = 0, ws_cursor = 0, ws_status = 0, ws_ctrl = 0;
     size_t ws_skeys = 0, ws_svals = 0, ws_hist = 0, ws_over_u = 0, ws_overp = 0, ws_overord = 0, ws_bytes = 0;
@@ -363,6 +366,7 @@ pb_status pb_spgemm_symbolic(pb_handle *h, const pb_csc *A, const pb_csr *B, pb_
         cuda_fail(h, e, "chunk table");
         return bail(PB_ERR_CUDA);
     }
+    p->packed = (tuple_val_bytes(dtype) == 4 && p->hdr.n_oversize == 0 && !(cfg && cfg->deterministic)) ? 1 : 0;
     // Deterministic mode: fixed run positions (CSC order inside each bin).
     if (cfg && cfg->deterministic && p->nnzA > 0) {
         p->apos_bytes = align256(8 * (size_t)p->nnzA);
@@ -561,6 +565,7 @@ static pb_status fill_numeric(pb_handle *h, const pb_plan *p, const pb_csc *A, c
     a.over_passes = p->over_passes;
     a.over_dense = p->over_dense;
     a.over_p = reinterpret_cast<int64_t *>(w + p->ws_overp);
+    a.packed = p->packed;
     return PB_OK;
 }
 
@@ -859,6 +864,8 @@ pb_status pb_debug_expand(pb_handle *h, const pb_plan *p, const pb_csc *A, const
 }
 
 size_t pb_debug_values_offset(const pb_plan *p) { return p ? p->ws_vals : 0; }
+
+int32_t pb_debug_tuple_layout(const pb_plan *p) { return p ? p->packed : 0; }
 
 pb_status pb_plan_status(const pb_plan *p, pb_stream_t stream_, pb_status *device_status) {
     if (!p || !device_status) return PB_ERR_INVALID_ARG;

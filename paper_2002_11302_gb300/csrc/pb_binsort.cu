@@ -20,6 +20,8 @@
 // Two kernels: k_binsort for single products (phases described above it) and
 // k_binsort_batch for batched products (bins of many products in one launch,
 // each bin writing into its own product's C).
+#include <type_traits>
+
 #include "pb_common.cuh"
 
 namespace pb {
@@ -396,11 +398,15 @@ __device__ void stream_oversize_bin(const NumericArgs &p, int64_t b, int32_t row
 //      then sum in position order, i.e. ascending k).  Row pointers are written
 //      where the row changes.
 // ---------------------------------------------------------------------------
-template <int CAP, int THREADS, class TV>
+// PACK: the bin arrives as packed {key, value bits} pairs (4-byte values) in
+// vin.  Phase A takes each pair into registers and phases C/D write the value
+// at the tuple's sorted position over the start of vin (as floats), so phase F
+// reads values in sorted order.  The radix path reads the pairs in place.
+template <int CAP, int THREADS, class TV, bool PACK = false>
 struct BinSmem {
     static constexpr int NW = THREADS / 32;
     uint32_t kin[CAP];     // the bin's keys (bulk copy), then its sorted keys
-    TV vin[CAP];           // the bin's values (bulk copy)
+    typename std::conditional<PACK, uint2, TV>::type vin[CAP];  // the bin's values or pairs (bulk copy)
     uint32_t pk[CAP];      // multi-tuple buckets: low key bits << log2(CAP) | position; radix: keys
     uint16_t fidx[CAP];    // position in the bin of each sorted tuple
     uint16_t sidx2[CAP];   // radix: positions
@@ -445,9 +451,19 @@ __device__ inline uint4 bucket_words(uint4 c, uint32_t s) {
     return o;
 }
 
-template <int CAP, int THREADS, class TV, class OV>
+// Value of the bin's tuple at position i (shared memory).
+template <class TV, class S>
+__device__ inline TV bin_value(const S &sm, int i) {
+    if constexpr (sizeof(sm.vin[0]) == 8 && sizeof(TV) == 4)
+        return __uint_as_float(sm.vin[i].y);  // packed pair
+    else
+        return sm.vin[i];
+}
+
+template <int CAP, int THREADS, class TV, class OV, bool PACK>
 __global__ void __launch_bounds__(THREADS, (THREADS <= 256 ? 4 : (THREADS <= 512 ? 2 : 1))) k_binsort(const NumericArgs p) {
-    using S = BinSmem<CAP, THREADS, TV>;
+    using S = BinSmem<CAP, THREADS, TV, PACK>;
+    static_assert(!PACK || sizeof(TV) == 4, "packed tuples hold 4-byte values");
     constexpr int NW = THREADS / 32;
     constexpr int E = CAP / THREADS;  // tuples per thread in A-D
     constexpr int WS = CAP / NW;      // sorted positions per warp in E-F
@@ -479,11 +495,17 @@ __global__ void __launch_bounds__(THREADS, (THREADS <= 256 ? 4 : (THREADS <= 512
         if (b >= p.bin_hi) break;
         const int32_t row0 = p.bin_row[b], row1 = p.bin_row[b + 1];
         const int64_t off = p.bin_off[b] - p.tuple_base;  // the buffer holds this panel's tuples
-        const int64_t Nfull = p.R[row1] - p.R[row0];
+        int64_t Nfull = p.R[row1] - p.R[row0];
         if (Nfull > CAP) {
-            stream_oversize_bin<THREADS, TV, OV>(p, b, row0, row1, off, Nfull, colmask, sm.scratch, &sm.prefix,
-                                                 &sm.ok);
-            continue;
+            if constexpr (PACK) {
+                // packed plans have no oversize bins; record it and skip the tuples
+                if (tid == 0) atomicOr(p.err, DEV_ERR_CAPACITY);
+                Nfull = 0;
+            } else {
+                stream_oversize_bin<THREADS, TV, OV>(p, b, row0, row1, off, Nfull, colmask, sm.scratch,
+                                                     &sm.prefix, &sm.ok);
+                continue;
+            }
         }
         int N = (int)Nfull;
         const int rows_b = row1 - row0;
@@ -492,9 +514,14 @@ __global__ void __launch_bounds__(THREADS, (THREADS <= 256 ? 4 : (THREADS <= 512
         if (N > 0) {
             if (tid == 0) {
                 const uint32_t n4 = (uint32_t)((N + 3) & ~3);
-                mbar_arrive_expect_tx(&sm.bar, n4 * 4u + n4 * (uint32_t)sizeof(TV));
-                bulk_g2s(sm.kin, p.keys + off, n4 * 4u, &sm.bar);
-                bulk_g2s(sm.vin, gvals + off, n4 * (uint32_t)sizeof(TV), &sm.bar);
+                if constexpr (PACK) {
+                    mbar_arrive_expect_tx(&sm.bar, n4 * 8u);
+                    bulk_g2s(sm.vin, reinterpret_cast<const uint2 *>(p.keys) + off, n4 * 8u, &sm.bar);
+                } else {
+                    mbar_arrive_expect_tx(&sm.bar, n4 * 4u + n4 * (uint32_t)sizeof(TV));
+                    bulk_g2s(sm.kin, p.keys + off, n4 * 4u, &sm.bar);
+                    bulk_g2s(sm.vin, gvals + off, n4 * (uint32_t)sizeof(TV), &sm.bar);
+                }
             }
             loaded = mbar_wait_bounded(&sm.bar, phase);
             phase ^= 1u;
@@ -507,28 +534,38 @@ __global__ void __launch_bounds__(THREADS, (THREADS <= 256 ? 4 : (THREADS <= 512
         }
         const uint32_t *sk = sm.kin;   // sorted keys
         const uint16_t *si = sm.fidx;  // their positions in the bin
+        float *sval = reinterpret_cast<float *>(sm.vin);  // PACK: values in sorted order (not radix)
+        bool radix = false;
         if (N > 0) {
             const uint32_t kmax = (uint32_t)((((uint64_t)rows_b) << colbits) - 1u);
             const int rbits = kmax ? 32 - __clz(kmax) : 0;
             const int shift = rbits > LOG_CAP ? rbits - LOG_CAP : 0;  // <= 32 - LOG_CAP
             const uint32_t lowmask = (1u << shift) - 1u;
             // ---- A: bucket counts and arrival ranks ------------------------------------
-            uint32_t kr[E], rk[E];
+            uint32_t kr[E], rk[E], vr[E];
             bool mine_big = false;
 #pragma unroll
             for (int j = 0; j < E; ++j) {
                 const int q = tid + j * THREADS;
                 kr[j] = 0;
                 rk[j] = 0;
+                vr[j] = 0;
                 if (q < N) {
-                    kr[j] = sm.kin[q];
+                    if constexpr (PACK) {
+                        const uint2 t = sm.vin[q];
+                        kr[j] = t.x;
+                        vr[j] = t.y;
+                    } else {
+                        kr[j] = sm.kin[q];
+                    }
                     rk[j] = atomicAdd(&sm.cnt[bucket_of(kr[j], shift, CAP)], 1u);
                     mine_big |= rk[j] >= SMALL_BUCKET;
                 }
             }
             if (mine_big) sm.big = 1;
             __syncthreads();
-            if (sm.big == 0) {
+            radix = sm.big != 0;
+            if (!radix) {
                 // ---- B: bucket starts ---------------------------------------------------
                 {
                     uint4 *c0 = reinterpret_cast<uint4 *>(sm.cnt + 4 * tid);
@@ -560,7 +597,10 @@ __global__ void __launch_bounds__(THREADS, (THREADS <= 256 ? 4 : (THREADS <= 512
                         const uint32_t start = w & 0xffffu;
                         if ((w >> 16) == 1u) {
                             sm.kin[start] = kr[j];
-                            sm.fidx[start] = (uint16_t)q;
+                            if constexpr (PACK)
+                                sval[start] = __uint_as_float(vr[j]);
+                            else
+                                sm.fidx[start] = (uint16_t)q;
                         } else {
                             sm.pk[start + rk[j]] = ((kr[j] & lowmask) << LOG_CAP) | (uint32_t)q;
                             multi |= 1u << j;
@@ -579,7 +619,10 @@ __global__ void __launch_bounds__(THREADS, (THREADS <= 256 ? 4 : (THREADS <= 512
                         int rank = start;
                         for (int r = start; r < end; ++r) rank += sm.pk[r] < mine;
                         sm.kin[rank] = kr[j];
-                        sm.fidx[rank] = (uint16_t)q;
+                        if constexpr (PACK)
+                            sval[rank] = __uint_as_float(vr[j]);
+                        else
+                            sm.fidx[rank] = (uint16_t)q;
                     }
                 }
                 __syncthreads();
@@ -600,7 +643,12 @@ __global__ void __launch_bounds__(THREADS, (THREADS <= 256 ? 4 : (THREADS <= 512
                     for (int j = 0; j < E; ++j) {
                         const int q = warp * WS + j * 32 + lane;
                         const bool valid = q < N;
-                        const uint32_t key = valid ? srck[q] : 0u;
+                        uint32_t key = 0u;
+                        if constexpr (PACK) {  // the first pass reads the packed input
+                            if (valid) key = srci ? srck[q] : sm.vin[q].x;
+                        } else {
+                            if (valid) key = srck[q];
+                        }
                         const uint32_t d = (key >> sh) & 255u;
                         uint32_t peers = __ballot_sync(FULL, valid);
 #pragma unroll
@@ -679,6 +727,13 @@ __global__ void __launch_bounds__(THREADS, (THREADS <= 256 ? 4 : (THREADS <= 512
         __syncthreads();
         if (!sm.ok) continue;
         // ---- F: merged entries and row pointers ---------------------------------------
+        // value of the tuple at sorted position i
+        auto value_at = [&](int i) -> double {
+            if constexpr (PACK)
+                return (double)(radix ? bin_value<TV>(sm, si[i]) : sval[i]);
+            else
+                return (double)bin_value<TV>(sm, si[i]);
+        };
         const int64_t P = sm.prefix;
         int64_t running = P + wbase;  // C position of the segment's first head
         uint32_t last = before;
@@ -707,18 +762,18 @@ __global__ void __launch_bounds__(THREADS, (THREADS <= 256 ? 4 : (THREADS <= 512
             if (hm == vm && ends) {
                 if (valid) {  // no duplicates: every tuple is its own entry
                     colidxC[idx] = (int32_t)(key & colmask);
-                    valC[idx] = (OV)(double)sm.vin[si[q]];
+                    valC[idx] = (OV)value_at(q);
                 }
             } else if (det || dups <= 4) {
                 if (head) {  // the run summed in sorted order from its head
-                    double acc = (double)sm.vin[si[q]];
-                    for (int r = q + 1; r < N && sk[r] == key; ++r) acc += (double)sm.vin[si[r]];
+                    double acc = value_at(q);
+                    for (int r = q + 1; r < N && sk[r] == key; ++r) acc += value_at(r);
                     colidxC[idx] = (int32_t)(key & colmask);
                     valC[idx] = (OV)acc;
                 }
             } else {
                 // segmented suffix sums: lane l adds lanes (l, end of its run in the chunk]
-                double v = valid ? (double)sm.vin[si[q]] : 0.0;
+                double v = valid ? value_at(q) : 0.0;
                 const uint32_t after = hm & ~lanemask_le();
                 const int endl = after ? __ffs(after) - 2 : 31;
 #pragma unroll
@@ -728,7 +783,7 @@ __global__ void __launch_bounds__(THREADS, (THREADS <= 256 ? 4 : (THREADS <= 512
                 }
                 if (head) {
                     if (endl == 31 && !ends)  // the run goes on past the chunk
-                        for (int r = qn; r < N && sk[r] == key; ++r) v += (double)sm.vin[si[r]];
+                        for (int r = qn; r < N && sk[r] == key; ++r) v += value_at(r);
                     colidxC[idx] = (int32_t)(key & colmask);
                     valC[idx] = (OV)v;
                 }
@@ -1096,10 +1151,10 @@ __global__ void __launch_bounds__(THREADS, (THREADS <= 256 ? 4 : (THREADS <= 512
     }
 }
 
-template <int CAP, int THREADS, class TV, class OV, bool BATCH>
+template <int CAP, int THREADS, class TV, class OV, bool BATCH, bool PACK = false>
 cudaError_t run_binsort(const NumericArgs &a, cudaStream_t s) {
-    auto kern = BATCH ? k_binsort_batch<CAP, THREADS, TV, OV, true> : k_binsort<CAP, THREADS, TV, OV>;
-    const size_t smem = BATCH ? sizeof(SortSmem<CAP, THREADS, TV>) : sizeof(BinSmem<CAP, THREADS, TV>);
+    auto kern = BATCH ? k_binsort_batch<CAP, THREADS, TV, OV, true> : k_binsort<CAP, THREADS, TV, OV, PACK>;
+    const size_t smem = BATCH ? sizeof(SortSmem<CAP, THREADS, TV>) : sizeof(BinSmem<CAP, THREADS, TV, PACK>);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
@@ -1115,12 +1170,12 @@ cudaError_t run_binsort(const NumericArgs &a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-template <class TV, class OV, bool BATCH>
+template <class TV, class OV, bool BATCH, bool PACK = false>
 cudaError_t dispatch_cap(const NumericArgs &a, cudaStream_t s) {
     switch (a.capacity) {
-        case 2048: return run_binsort<2048, 256, TV, OV, BATCH>(a, s);
-        case 4096: return run_binsort<4096, 512, TV, OV, BATCH>(a, s);
-        case 8192: return run_binsort<8192, 1024, TV, OV, BATCH>(a, s);
+        case 2048: return run_binsort<2048, 256, TV, OV, BATCH, PACK>(a, s);
+        case 4096: return run_binsort<4096, 512, TV, OV, BATCH, PACK>(a, s);
+        case 8192: return run_binsort<8192, 1024, TV, OV, BATCH, PACK>(a, s);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -1128,6 +1183,13 @@ cudaError_t dispatch_cap(const NumericArgs &a, cudaStream_t s) {
 template <bool BATCH>
 cudaError_t dispatch_dtype(const NumericArgs &a, cudaStream_t s) {
     if (a.bin_hi <= a.bin_lo) return cudaSuccess;
+    if (!BATCH && a.packed) {
+        switch (a.dtype) {
+            case PB_F32: return dispatch_cap<float, float, false, true>(a, s);
+            case PB_F64_F32TUPLE: return dispatch_cap<float, double, false, true>(a, s);
+            default: return cudaErrorInvalidValue;
+        }
+    }
     switch (a.dtype) {
         case PB_F64: return dispatch_cap<double, double, BATCH>(a, s);
         case PB_F32: return dispatch_cap<float, float, BATCH>(a, s);

@@ -380,6 +380,10 @@ struct NumericArgs {
     int64_t *over_p;    // [n_over] C offset of each oversize row, written by the sort kernel
     // deterministic mode: the first tuple position of each A entry's run (null: atomic cursors)
     const int64_t *apos;
+    // packed tuples (4-byte values only): tuple t is the 8-byte pair {key, value
+    // bits} at keys[2t], keys[2t + 1]; the pairs fill the key and value regions
+    // and `vals` is unused
+    int packed;
     // batched products (null for a single product)
     const BatchDesc *desc;
     const int32_t *chunk_prod;  // [nchunks] product of each expand work item

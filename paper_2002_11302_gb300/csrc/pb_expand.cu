@@ -129,7 +129,15 @@ struct RunDesc {  // a short run of the flattened stream, indexed by run order
 // arrays of the item's product are taken from its descriptor.
 // DET: runs go to positions fixed in the plan (deterministic mode) instead of
 // being reserved at the bins' cursors.
-template <class IV, class TV, bool BATCH, bool DET>
+// PACK: 4-byte values written with their keys as one 8-byte pair per tuple
+// (one store, half the scattered write requests of separate key and value arrays).
+template <class TV>
+__device__ inline uint2 packed_tuple(uint32_t key, TV v) {
+    static_assert(sizeof(TV) == 4, "packed tuples hold 4-byte values");
+    return make_uint2(key, __float_as_uint((float)v));
+}
+
+template <class IV, class TV, bool BATCH, bool DET, bool PACK>
 __global__ void __launch_bounds__(EXP_THREADS, PB_EXPAND_MINB) k_expand(const NumericArgs p) {
     __shared__ RunDesc sdesc[EXP_WARPS][32];
     __shared__ IV sav[EXP_WARPS][32];
@@ -143,6 +151,7 @@ __global__ void __launch_bounds__(EXP_THREADS, PB_EXPAND_MINB) k_expand(const Nu
     // buffer holds this panel's tuples from tuple_base on
     uint32_t *__restrict__ keys = p.keys - p.tuple_base;
     TV *__restrict__ vals = static_cast<TV *>(p.vals) - p.tuple_base;
+    uint2 *__restrict__ tup = reinterpret_cast<uint2 *>(p.keys) - p.tuple_base;  // PACK
     int64_t nchunks = p.nchunks;
     if constexpr (BATCH) {
         if (*p.err & DEV_ERR_BATCH_FATAL) return;
@@ -232,8 +241,13 @@ __global__ void __launch_bounds__(EXP_THREADS, PB_EXPAND_MINB) k_expand(const Nu
                 for (int u = 0; u < PB_EXPAND_U; ++u) {
                     const int32_t t = t0 + 32 * u + lane;
                     if (t < total && d[u].poff != NO_POS) {
-                        keys[d[u].poff + t] = d[u].keyhi | col[u];
-                        vals[d[u].poff + t] = tuple_product<TV, IV>(avs[r[u]], bv[u]);
+                        const TV v = tuple_product<TV, IV>(avs[r[u]], bv[u]);
+                        if constexpr (PACK) {
+                            tup[d[u].poff + t] = packed_tuple<TV>(d[u].keyhi | col[u], v);
+                        } else {
+                            keys[d[u].poff + t] = d[u].keyhi | col[u];
+                            vals[d[u].poff + t] = v;
+                        }
                     }
                 }
             }
@@ -249,8 +263,14 @@ __global__ void __launch_bounds__(EXP_THREADS, PB_EXPAND_MINB) k_expand(const Nu
                 const int64_t pr = __shfl_sync(FULL, cur_pos, rl);
                 if (pr == NO_POS) continue;
                 for (int32_t ib = lane; ib < lr; ib += 32) {
-                    keys[pr + ib] = keyhi | (uint32_t)colidxB[br + ib];
-                    vals[pr + ib] = tuple_product<TV, IV>(ar, valB[br + ib]);
+                    const uint32_t key = keyhi | (uint32_t)colidxB[br + ib];
+                    const TV v = tuple_product<TV, IV>(ar, valB[br + ib]);
+                    if constexpr (PACK) {
+                        tup[pr + ib] = packed_tuple<TV>(key, v);
+                    } else {
+                        keys[pr + ib] = key;
+                        vals[pr + ib] = v;
+                    }
                 }
             }
             __syncwarp();  // the descriptors are rewritten by the next batch
@@ -261,9 +281,9 @@ __global__ void __launch_bounds__(EXP_THREADS, PB_EXPAND_MINB) k_expand(const Nu
     }
 }
 
-template <class IV, class TV, bool BATCH, bool DET>
+template <class IV, class TV, bool BATCH, bool DET, bool PACK = false>
 cudaError_t run_expand(const NumericArgs &a, cudaStream_t s) {
-    auto kern = k_expand<IV, TV, BATCH, DET>;
+    auto kern = k_expand<IV, TV, BATCH, DET, PACK>;
     int per_sm = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, EXP_THREADS, 0);
     if (e != cudaSuccess) return e;
@@ -291,6 +311,13 @@ cudaError_t dispatch_expand(const NumericArgs &a, cudaStream_t s) {
 
 cudaError_t launch_expand(const NumericArgs &a, cudaStream_t s) {
     if (a.flop <= 0) return cudaSuccess;
+    if (a.packed) {
+        switch (a.dtype) {
+            case PB_F32: return run_expand<float, float, false, false, true>(a, s);
+            case PB_F64_F32TUPLE: return run_expand<double, float, false, false, true>(a, s);
+            default: return cudaErrorInvalidValue;
+        }
+    }
     return a.apos ? dispatch_expand<false, true>(a, s) : dispatch_expand<false, false>(a, s);
 }
 

@@ -42,6 +42,31 @@ def test_tiny_random_rectangular(pb, seed):
     assert_matches(C, oracle.spgemm(A, B), EPS["f64"])
 
 
+@pytest.mark.parametrize("cap", [2048, 4096, 8192])
+@pytest.mark.parametrize("dtype", [0, 1, 2])
+def test_bins_with_many_equal_keys(pb, cap, dtype):
+    """Rows of 40 x 8 tuples on only 8 columns: every (row, column) key repeats
+    about 40 times, above the 32 tuples a bucket takes before a bin falls back to
+    the in-bin radix sort.  FP64, FP32 and FP32 tuples (the 4-byte forms read the
+    packed {key, value} pairs), at every bin capacity."""
+    rng = np.random.default_rng(80 + cap + dtype)
+    m, k, n = 300, 200, 8
+    rows = np.repeat(np.arange(m), 40)
+    cols = np.concatenate([rng.choice(k, 40, replace=False) for _ in range(m)])
+    A = synth.coo_to_csc(m, k, rows, cols, rng.uniform(-1, 1, rows.size))
+    Bd = rng.uniform(-1, 1, (k, n))
+    r, c = np.nonzero(Bd)
+    B = synth.coo_to_csr(k, n, r, c, Bd[r, c])
+    vdt = None
+    if dtype == 1:
+        A = synth.CSC(A.nrows, A.ncols, A.colptr, A.rowidx, A.val.astype(np.float32))
+        B = synth.CSR(B.nrows, B.ncols, B.rowptr, B.colidx, B.val.astype(np.float32))
+        vdt = torch.float32
+    assert int(np.max(oracle.row_flop(A, B))) <= 2048
+    C = run(pb, A, B, dtype=dtype, cap=cap, vdt=vdt)
+    assert_matches(C, oracle.spgemm(A, B), EPS["f64"] if dtype == 0 else EPS["f32"])
+
+
 def test_er_4096_d4(pb):
     A, B = synth.er(4096, 4, seed=0)
     C = run(pb, A, B)
@@ -309,6 +334,44 @@ def test_expand_tuples_match_oracle_expansion(pb):
     assert np.array_equal(np.concatenate(rows)[got], er[exp].astype(np.int64))
     assert np.array_equal(np.concatenate(cols)[got], ec[exp].astype(np.int64))
     assert np.array_equal(np.concatenate(vs)[got], ev[exp])       # one rounding each: bit-exact
+
+
+@pytest.mark.parametrize("dtype", ["PB_F32", "PB_F64_F32TUPLE"])
+def test_expand_packed_tuples_match_oracle_expansion(pb, dtype):
+    """4-byte tuple values are written as packed {key, value bits} pairs; the
+    expanded multiset matches the oracle's with each product rounded once to
+    FP32 (PB_F32: FP32 inputs; PB_F64_F32TUPLE: the FP64 product rounded)."""
+    A, B = synth.er(6000, 6, seed=32, shuffle_within=True)
+    f32 = dtype == "PB_F32"
+    if f32:
+        A = synth.CSC(A.nrows, A.ncols, A.colptr, A.rowidx, A.val.astype(np.float32))
+        B = synth.CSR(B.nrows, B.ncols, B.rowptr, B.colidx, B.val.astype(np.float32))
+    vdt = torch.float32 if f32 else torch.float64
+    Ad, Bd = pb.csc_to_device(A, val_dtype=vdt), pb.csr_to_device(B, val_dtype=vdt)
+    plan = pb.symbolic(Ad, Bd, dtype=getattr(pb, dtype))
+    assert pb.debug_tuple_layout(plan) == 1
+    ws = plan.workspace()
+    ws, _ = pb.debug_expand(plan, Ad, Bd, ws)
+    torch.cuda.synchronize()
+    _, R, bin_row, bin_off = (t.cpu().numpy() for t in plan.export())
+    pairs = ws.cpu().numpy()[: 8 * int(bin_off[-1])].view(np.uint32).reshape(-1, 2)
+    colbits = max(1, int(np.ceil(np.log2(max(B.ncols, 2)))))
+    rows, cols, vs = [], [], []
+    for b in range(plan.nbins):
+        cnt = int(R[bin_row[b + 1]] - R[bin_row[b]])
+        k = pairs[bin_off[b]: bin_off[b] + cnt, 0]
+        r = bin_row[b] + (k >> colbits).astype(np.int64)
+        assert np.all(r < bin_row[b + 1]), "tuple outside its bin's row range"
+        rows.append(r)
+        cols.append((k & ((1 << colbits) - 1)).astype(np.int64))
+        vs.append(pairs[bin_off[b]: bin_off[b] + cnt, 1].view(np.float32))
+    got = np.lexsort((np.concatenate(vs), np.concatenate(cols), np.concatenate(rows)))
+    er, ec, ev = oracle.expand(A, B)
+    ev32 = ev.astype(np.float32)
+    exp = np.lexsort((ev32, ec, er))
+    assert np.array_equal(np.concatenate(rows)[got], er[exp].astype(np.int64))
+    assert np.array_equal(np.concatenate(cols)[got], ec[exp].astype(np.int64))
+    assert np.array_equal(np.concatenate(vs)[got], ev32[exp])     # one FP32 rounding of the product
 
 
 def test_capacity_overflow_reported(pb):
