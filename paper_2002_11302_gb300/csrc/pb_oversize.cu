@@ -389,6 +389,161 @@ __global__ void __launch_bounds__(DT) k_over_dense(const OversizeArgs a, int gro
     }
 }
 
+// Position of the r-th (from 0) set bit of x; x has more than r set bits.
+__device__ inline uint32_t select_bit(uint32_t x, uint32_t r) {
+    uint32_t pos = 0, c = __popc(x & 0xffffu);
+    if (r >= c) { r -= c; x >>= 16; pos += 16; }
+    c = __popc(x & 0xffu);
+    if (r >= c) { r -= c; x >>= 8; pos += 8; }
+    c = __popc(x & 0xfu);
+    if (r >= c) { r -= c; x >>= 4; pos += 4; }
+    c = __popc(x & 0x3u);
+    if (r >= c) { r -= c; x >>= 2; pos += 2; }
+    if (r >= (x & 1u)) pos += 1;
+    return pos;
+}
+
+// First round at or after digit d that holds tuples (256 when none is left).
+__device__ inline int next_round(const int64_t *offs, int d, int group) {
+    while (d < 256 && offs[d] >= offs[min(d + group, 256)]) d += group;
+    return d;
+}
+
+constexpr int DPF = 4;  // tuples per thread of the next round loaded during a compaction
+
+// The dense tiles for rounds of at most 8192 columns, with a presence bitmap
+// (one 32-column word per thread) instead of a flag per column.  Compaction
+// costs what the round holds, not the tile width: the words' set-bit counts
+// are scanned, and output entry j (written by thread j mod DT, so the stores
+// are coalesced) finds its word by binary search over the prefix and its
+// column by selecting the bit.  The first tuples of the next round are loaded
+// into registers before the compaction, so their latency overlaps it.  (R-MAT
+// hub rows spread over many sparse rounds: at scale 20 a 4096-column round
+// holds a few hundred tuples.)
+template <class TV>
+__global__ void __launch_bounds__(DT) k_over_dense_bm(const OversizeArgs a, int group) {
+    extern __shared__ __align__(16) unsigned char sraw[];
+    const int w = a.dense_shift;
+    const int W = group << w;  // a round covers `group` consecutive digits; W <= 8192
+    const int NWORD = W >> 5;  // <= DT
+    constexpr int NWD = DT / 32;
+    double *acc = reinterpret_cast<double *>(sraw);
+    int64_t *offs = reinterpret_cast<int64_t *>(acc + W);      // [257] segment starts of the row
+    uint32_t *bm = reinterpret_cast<uint32_t *>(offs + 264);   // [NWORD] columns touched by the round
+    uint32_t *bmc = bm + DT;                                   // [NWORD] the round's words, for the compaction
+    uint32_t *pre = bmc + DT;                                  // [NWORD + 1] set bits before each word
+    uint32_t *wsum = pre + DT + 8;                             // [NWD] per-warp totals of the word scan
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    for (int i = tid; i < W; i += DT) acc[i] = 0.0;
+    if (tid < NWORD) bm[tid] = 0;
+    const int64_t o_hi = over_o_hi(a);
+    __shared__ int64_t next_row;
+    while (true) {
+        // rows are taken through a ticket, largest size class first
+        if (tid == 0) {
+            const int64_t t = (int64_t)atomicAdd(&a.row_ticket[0], 1u);
+            next_row = t < o_hi - a.o_lo ? a.o_lo + a.row_order[t] : o_hi;
+        }
+        __syncthreads();
+        const int64_t o = next_row;
+        if (o >= o_hi) break;
+        const int64_t bin = a.over_bin[o];
+        const int64_t N = a.R[a.bin_row[bin + 1]] - a.R[a.bin_row[bin]];
+        const int64_t c0 = a.over_chunk_off[o] - a.c_lo;  // the bin's first work item holds its digit offsets
+        offs[tid] = over_hist(a)[c0 * 256 + tid];
+        if (tid == 0) offs[256] = N;
+        __syncthreads();
+        uint32_t *xk = a.skeys + (a.over_tuple_off[o] - a.over_base);
+        TV *xv = static_cast<TV *>(a.svals) + (a.over_tuple_off[o] - a.over_base);
+        // FP64 merged values of FP32 tuples: the row's main-buffer region (see OversizeArgs::wide)
+        const int64_t half = (N + 1) / 2;
+        double *wa = reinterpret_cast<double *>(a.keys + (a.bin_off[bin] - a.tuple_base));
+        double *wb = reinterpret_cast<double *>(static_cast<TV *>(a.vals) + (a.bin_off[bin] - a.tuple_base));
+        int64_t run = 0;  // merged entries written so far (the row's output is compacted to its start)
+        uint32_t pk[DPF];
+        TV pv[DPF];
+        auto prefetch = [&](int d) {
+#pragma unroll
+            for (int j = 0; j < DPF; ++j) {
+                const int64_t q = offs[d] + j * DT + tid;
+                if (d < 256 && q < offs[min(d + group, 256)]) {
+                    pk[j] = xk[q];
+                    pv[j] = xv[q];
+                }
+            }
+        };
+        int d = next_round(offs, 0, group);
+        prefetch(d);
+        while (d < 256) {
+            const int64_t start = offs[d], end = offs[min(d + group, 256)];
+            const uint32_t base = (uint32_t)d << w;
+#pragma unroll
+            for (int j = 0; j < DPF; ++j) {
+                if (start + j * DT + tid < end) {
+                    const uint32_t loc = pk[j] - base;
+                    atomicAdd(&acc[loc], (double)pv[j]);
+                    atomicOr(&bm[loc >> 5], 1u << (loc & 31u));
+                }
+            }
+            for (int64_t q = start + DPF * DT + tid; q < end; q += DT) {
+                const uint32_t loc = xk[q] - base;
+                atomicAdd(&acc[loc], (double)xv[q]);
+                atomicOr(&bm[loc >> 5], 1u << (loc & 31u));
+            }
+            // the next round's first tuples lie past this round's end, where no output goes
+            const int d2 = next_round(offs, d + group, group);
+            prefetch(d2);
+            __syncthreads();
+            // compaction: exclusive scan of the words' set-bit counts
+            uint32_t c = 0;
+            if (tid < NWORD) {
+                const uint32_t bits = bm[tid];
+                bm[tid] = 0;
+                bmc[tid] = bits;
+                c = (uint32_t)__popc(bits);
+            }
+            const uint32_t inc = warp_inclusive_scan(c);
+            if (lane == 31) wsum[wid] = inc;
+            __syncthreads();
+            uint32_t wbase = 0, tot = 0;
+#pragma unroll
+            for (int k = 0; k < NWD; ++k) {
+                const uint32_t t = wsum[k];
+                wbase += (k < wid) ? t : 0u;
+                tot += t;
+            }
+            if (tid < NWORD) pre[tid] = wbase + inc - c;
+            if (tid == 0) pre[NWORD] = tot;
+            __syncthreads();
+            // output positions never pass the round's own end: run + tot <= end
+            for (uint32_t j = tid; j < tot; j += DT) {
+                int lo = 0, hi = NWORD;  // pre[lo] <= j < pre[hi]
+                while (hi - lo > 1) {
+                    const int mid = (lo + hi) >> 1;
+                    if (pre[mid] <= j)
+                        lo = mid;
+                    else
+                        hi = mid;
+                }
+                const uint32_t col = ((uint32_t)lo << 5) + select_bit(bmc[lo], j - pre[lo]);
+                const int64_t pos = run + j;
+                xk[pos] = base + col;
+                if (a.wide)
+                    *(pos < half ? wa + pos : wb + (pos - half)) = acc[col];
+                else
+                    xv[pos] = (TV)acc[col];
+                acc[col] = 0.0;
+            }
+            run += tot;
+            d = d2;
+            __syncthreads();  // the tile is clear and the words are free for the next round
+        }
+        if (tid == 0) a.over_u[o] = run;
+        // every thread has read this row's offsets and its ticket before the next row's are stored
+        __syncthreads();
+    }
+}
+
 // Columns of one dense round: consecutive digits grouped up to this width.
 constexpr int DENSE_ROUND_COLUMNS = 4096;
 
@@ -398,8 +553,11 @@ cudaError_t run_dense(const OversizeArgs &a, int num_sms, cudaStream_t s) {
     if (group < 1) group = 1;
     if (group > 256) group = 256;
     const int W = group << a.dense_shift;
-    const size_t smem = 8 * (size_t)W + 8 * (264 + 40) + 4 * (size_t)DENSE_WCNT + (size_t)((W + 15) & ~15);
-    auto kern = k_over_dense<TV>;
+    // rounds of up to 8192 columns use the bitmap form (one word per thread)
+    const bool bitmap = W <= 32 * DT;
+    const size_t smem = bitmap ? 8 * (size_t)W + 8 * 264 + 4 * (3 * (size_t)DT + 8 + 32)
+                               : 8 * (size_t)W + 8 * (264 + 40) + 4 * (size_t)DENSE_WCNT + (size_t)((W + 15) & ~15);
+    auto kern = bitmap ? k_over_dense_bm<TV> : k_over_dense<TV>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
