@@ -357,6 +357,12 @@ pb_status pb_batch_set_tuning(pb_handle *h, const pb_batch_tune *entries, int32_
  *                    A (n x n, CSC) in `A`, the prolongator P (n x nc, CSR) in
  *                    `B`.  Two products: AP = A * P (CSR), then P^T * AP with
  *                    P^T taken as the CSC view of P's CSR arrays.
+ * Small requests are coalesced: a slot that admits a request of at most
+ * 2^24 estimated work also takes the other queued requests that small with the
+ * same dtype (16 in all at most; pb_server_set_batching changes both) and runs
+ * them as one pb_spgemm_batch launch (Galerkin members: one launch for all
+ * A P, one for all P^T (A P)), with flop-sized results.  A group that cannot
+ * run batched runs its requests one by one.
  * A request whose need exceeds the whole budget completes with PB_ERR_BUSY.
  * No request is admitted while an admitted one waits for memory.  When every
  * admitted request is waiting for memory, the most recently admitted one is
@@ -398,6 +404,13 @@ pb_status pb_serve_release(pb_server *s, uint64_t req_id);
 /* Counters: requests completed and preempted, bytes held now and at most. */
 pb_status pb_serve_stats(pb_server *s, int64_t *completed, int64_t *preempted, size_t *bytes_in_use,
                          size_t *peak_bytes);
+/* Coalescing of small requests: at most max_requests per batched launch (1
+ * turns coalescing off), requests of at most max_request_work estimated work
+ * (nnz(A) times the mean row length of B, per product).  Applies to later
+ * admissions.  Errors: INVALID_ARG. */
+pb_status pb_server_set_batching(pb_server *s, int32_t max_requests, double max_request_work);
+/* Requests completed through batched launches, and those launches. */
+pb_status pb_serve_batch_stats(pb_server *s, int64_t *requests, int64_t *launches);
 
 /*
  * No-allocation entry point (the paper has no counterpart; this serves callers).

@@ -124,6 +124,8 @@ SIGNATURES = {
     "pb_serve_release": (ctypes.c_int, [_VP, ctypes.c_uint64]),
     "pb_serve_stats": (ctypes.c_int, [_VP, ctypes.POINTER(_I64), ctypes.POINTER(_I64), ctypes.POINTER(_SZ),
                                       ctypes.POINTER(_SZ)]),
+    "pb_server_set_batching": (ctypes.c_int, [_VP, _I32, ctypes.c_double]),
+    "pb_serve_batch_stats": (ctypes.c_int, [_VP, ctypes.POINTER(_I64), ctypes.POINTER(_I64)]),
 }
 
 _lib = None
@@ -617,7 +619,15 @@ class Server:
         c, p, u, k = _I64(), _I64(), _SZ(), _SZ()
         _check(self.lib, self.handle.ptr, self.lib.pb_serve_stats(self.ptr, ctypes.byref(c), ctypes.byref(p),
                                                                   ctypes.byref(u), ctypes.byref(k)))
-        return {"completed": c.value, "preempted": p.value, "bytes_in_use": u.value, "peak_bytes": k.value}
+        br, bl = _I64(), _I64()
+        _check(self.lib, self.handle.ptr, self.lib.pb_serve_batch_stats(self.ptr, ctypes.byref(br), ctypes.byref(bl)))
+        return {"completed": c.value, "preempted": p.value, "bytes_in_use": u.value, "peak_bytes": k.value,
+                "batched_requests": br.value, "batch_launches": bl.value}
+
+    def set_batching(self, max_requests: int, max_request_work: float) -> None:
+        """Coalesce up to max_requests queued requests of at most max_request_work estimated work per launch."""
+        _check(self.lib, self.handle.ptr, self.lib.pb_server_set_batching(self.ptr, max_requests,
+                                                                          float(max_request_work)))
 
     def close(self) -> None:
         if getattr(self, "ptr", None):

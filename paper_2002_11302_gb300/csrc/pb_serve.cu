@@ -12,6 +12,13 @@
 // goes first (nnz(A) times the mean row length of B), unless the oldest has
 // been passed over MAX_BYPASS times already.
 //
+// Small requests are coalesced: a slot that admits a request of at most
+// `batch_work` estimated work also takes the other queued small requests of
+// the same value type (up to `batch_max` in all) and runs them as one batched
+// launch (pb_spgemm_batch; a Galerkin group as two: A P for all members, then
+// P^T (A P)).  If the group cannot run as a batch (its need exceeds the
+// budget, a device error), its members run one by one.
+//
 // Every device byte the server holds (plans, workspaces, intermediates and
 // results) comes from the server's own memory pool and is counted against the
 // budget before it is allocated.  A slot that lacks memory waits; no new
@@ -82,6 +89,9 @@ struct pb_server {
     int waiting = 0;  // slots waiting for memory
     uint64_t next_id = 1;
     int64_t completed = 0, preempted = 0;
+    int batch_max = 16;                   // requests per coalesced launch (1: no coalescing)
+    double batch_work = (double)(1 << 24);  // largest estimated work of a coalesced request
+    int64_t batched_requests = 0, batch_launches = 0;
 };
 
 namespace {
@@ -354,6 +364,167 @@ Outcome run(pb_server *S, int slot, Req *q, pb_status *status) {
     return OK_DONE;
 }
 
+// ---- coalesced small requests -----------------------------------------------
+// One batched launch: the products of a group's members and their results.
+struct BatchStep {
+    std::vector<Req *> owner;
+    std::vector<pb_csc> A;
+    std::vector<pb_csr> B;
+    std::vector<bool> rp32;  // int32 row pointers (an intermediate AP)
+    std::vector<Buf> rowptr, colidx, val;
+    std::vector<int64_t> nnz;
+    void add(Req *q, const pb_csc &a, const pb_csr &b, bool r32) {
+        owner.push_back(q);
+        A.push_back(a);
+        B.push_back(b);
+        rp32.push_back(r32);
+    }
+};
+
+void drop_step(pb_server *S, cudaStream_t s, BatchStep &st) {
+    for (auto *v : {&st.rowptr, &st.colidx, &st.val})
+        for (Buf &b : *v) put(S, s, b);
+}
+
+// Run a batch step: reserve, allocate, launch, read the statuses and nnz.
+Outcome run_batch_step(pb_server *S, int slot, Req *primary, int32_t dtype, BatchStep &st, pb_status *status) {
+    pb_handle *hd = S->hs[slot];
+    cudaStream_t s = S->streams[slot];
+    pb_stream_t ps = reinterpret_cast<pb_stream_t>(s);
+    const int32_t n = (int32_t)st.A.size();
+    const size_t vb = val_bytes(dtype);
+    // the query's temporary index arrays, counted by the plans' estimate
+    size_t est = 0;
+    for (const pb_csc &a : st.A) est += plan_estimate(a);
+    if (est > S->budget) {
+        *status = PB_ERR_BUSY;
+        return FAILED;
+    }
+    if (!wait_reserve(S, primary, est)) return PREEMPTED;
+    std::vector<int64_t> flop((size_t)n, 0);
+    size_t ws_bytes = 0;
+    pb_status e = pb_spgemm_batch_query(hd, n, st.A.data(), st.B.data(), (pb_dtype)dtype, ps, &ws_bytes, flop.data(),
+                                        nullptr);
+    unreserve(S, est);
+    if (e != PB_OK) {
+        *status = e;
+        return FAILED;
+    }
+    auto out_bytes = [&](int32_t i) {
+        const size_t c = (size_t)std::max<int64_t>(flop[(size_t)i], 1);
+        return r256((st.rp32[(size_t)i] ? 4 : 8) * ((size_t)st.A[(size_t)i].nrows + 1)) + r256(4 * c) + r256(vb * c);
+    };
+    size_t need = r256(ws_bytes) + r256(8 * (size_t)n) + 256;
+    for (int32_t i = 0; i < n; ++i) need += out_bytes(i);
+    if (need > S->budget) {
+        *status = PB_ERR_BUSY;
+        return FAILED;
+    }
+    if (!wait_reserve(S, primary, need)) return PREEMPTED;
+    size_t left = need;
+    Buf ws, nnz, dstat;
+    st.rowptr.assign((size_t)n, Buf{});
+    st.colidx.assign((size_t)n, Buf{});
+    st.val.assign((size_t)n, Buf{});
+    auto release = [&]() {
+        (void)cudaStreamSynchronize(s);
+        unreserve(S, left);
+        left = 0;
+        for (Buf *b : {&ws, &nnz, &dstat}) put(S, s, *b);
+    };
+    pb_status a = PB_OK;
+    if ((a = alloc(S, s, ws, r256(ws_bytes), &left)) != PB_OK || (a = alloc(S, s, nnz, r256(8 * (size_t)n), &left)) != PB_OK ||
+        (a = alloc(S, s, dstat, 256, &left)) != PB_OK) {
+        release();
+        drop_step(S, s, st);
+        *status = a;
+        return FAILED;
+    }
+    std::vector<pb_csr_out> C((size_t)n);
+    for (int32_t i = 0; i < n && a == PB_OK; ++i) {
+        const size_t k = (size_t)i, c = (size_t)std::max<int64_t>(flop[k], 1);
+        if ((a = alloc(S, s, st.rowptr[k], r256((st.rp32[k] ? 4 : 8) * ((size_t)st.A[k].nrows + 1)), &left)) != PB_OK ||
+            (a = alloc(S, s, st.colidx[k], r256(4 * c), &left)) != PB_OK ||
+            (a = alloc(S, s, st.val[k], r256(vb * c), &left)) != PB_OK)
+            break;
+        C[k] = pb_csr_out{st.A[k].nrows, st.B[k].ncols, flop[k],
+                          st.rp32[k] ? nullptr : static_cast<int64_t *>(st.rowptr[k].p),
+                          st.rp32[k] ? static_cast<int32_t *>(st.rowptr[k].p) : nullptr,
+                          static_cast<int32_t *>(st.colidx[k].p), st.val[k].p, static_cast<int64_t *>(nnz.p) + i};
+    }
+    int32_t dev = PB_OK;
+    st.nnz.assign((size_t)n, 0);
+    if (a == PB_OK)
+        a = pb_spgemm_batch(hd, n, st.A.data(), st.B.data(), C.data(), (pb_dtype)dtype, ws.p, ws.bytes, ps,
+                            static_cast<int32_t *>(dstat.p));
+    if (a == PB_OK && (cudaMemcpyAsync(&dev, dstat.p, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+                       cudaMemcpyAsync(st.nnz.data(), nnz.p, 8 * (size_t)n, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+                       cudaStreamSynchronize(s) != cudaSuccess))
+        a = PB_ERR_CUDA;
+    if (a == PB_OK) a = (pb_status)dev;
+    release();
+    if (a != PB_OK) {
+        drop_step(S, s, st);
+        *status = a;
+        return FAILED;
+    }
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        ++S->batch_launches;
+    }
+    return OK_DONE;
+}
+
+// Run a group of small requests as batched launches.  On success every member
+// owns its final C; otherwise nothing is held.
+Outcome run_group(pb_server *S, int slot, std::vector<Req *> &g, pb_status *status) {
+    cudaStream_t s = S->streams[slot];
+    const int32_t dtype = g[0]->r.dtype;
+    BatchStep s1, s2;
+    for (Req *q : g) s1.add(q, q->r.A, q->r.B, q->r.kind == PB_REQ_GALERKIN);  // Galerkin: AP = A * P
+    Outcome o = run_batch_step(S, slot, g[0], dtype, s1, status);
+    if (o != OK_DONE) return o;
+    for (size_t i = 0; i < g.size(); ++i) {
+        const pb_request &r = g[i]->r;
+        if (r.kind != PB_REQ_GALERKIN) continue;
+        // P^T as CSC is P's CSR arrays read column-wise; AP is step 1's C
+        s2.add(g[i], pb_csc{r.B.ncols, r.B.nrows, r.B.nnz, r.B.rowptr, r.B.colidx, r.B.val},
+               pb_csr{r.A.nrows, r.B.ncols, s1.nnz[i], static_cast<const int32_t *>(s1.rowptr[i].p),
+                      static_cast<const int32_t *>(s1.colidx[i].p), s1.val[i].p},
+               false);
+    }
+    if (!s2.A.empty()) {
+        o = run_batch_step(S, slot, g[0], dtype, s2, status);
+        // the intermediates AP are no longer needed either way
+        (void)cudaStreamSynchronize(s);
+        for (size_t i = 0; i < g.size(); ++i)
+            if (g[i]->r.kind == PB_REQ_GALERKIN)
+                for (Buf *b : {&s1.rowptr[i], &s1.colidx[i], &s1.val[i]}) put(S, s, *b);
+        if (o != OK_DONE) {
+            drop_step(S, s, s1);
+            return o;
+        }
+    }
+    size_t j = 0;
+    for (size_t i = 0; i < g.size(); ++i) {
+        Req *q = g[i];
+        if (q->r.kind == PB_REQ_GALERKIN) {
+            q->out_rowptr = s2.rowptr[j];
+            q->out_colidx = s2.colidx[j];
+            q->out_val = s2.val[j];
+            q->nnz = s2.nnz[j];
+            ++j;
+        } else {
+            q->out_rowptr = s1.rowptr[i];
+            q->out_colidx = s1.colidx[i];
+            q->out_val = s1.val[i];
+            q->nnz = s1.nnz[i];
+        }
+    }
+    *status = PB_OK;
+    return OK_DONE;
+}
+
 void slot_main(SlotCtx c) {
     pb_server *S = c.S;
     const int slot = c.slot;
@@ -374,23 +545,70 @@ void slot_main(SlotCtx c) {
         Req *q = S->queue[pick];
         for (size_t i = 0; i < pick; ++i) ++S->queue[i]->bypassed;
         S->queue.erase(S->queue.begin() + (std::ptrdiff_t)pick);
+        // a small request takes the other queued small requests of its value type along
+        std::vector<Req *> group{q};
+        if (S->batch_max > 1 && q->est <= S->batch_work) {
+            for (size_t i = 0; i < S->queue.size() && (int)group.size() < S->batch_max;) {
+                Req *x = S->queue[i];
+                if (x->est <= S->batch_work && x->r.dtype == q->r.dtype) {
+                    group.push_back(x);
+                    S->queue.erase(S->queue.begin() + (std::ptrdiff_t)i);
+                } else {
+                    ++i;
+                }
+            }
+        }
         S->active[slot] = q;
-        q->preempt = false;
-        q->t_admit = Clock::now();
-        if (!q->admitted_once) {
-            q->admitted_once = true;
-            q->t_first_admit = q->t_admit;
+        const Clock::time_point now = Clock::now();
+        for (Req *x : group) {
+            x->preempt = false;
+            x->t_admit = now;
+            if (!x->admitted_once) {
+                x->admitted_once = true;
+                x->t_first_admit = now;
+            }
         }
         lk.unlock();
-        pb_status st = PB_OK;
-        const Outcome o = run(S, slot, q, &st);
-        if (o != PREEMPTED) finish(S, q, st);
+        std::vector<Req *> requeue;
+        if (group.size() > 1) {
+            pb_status st = PB_OK;
+            const Outcome o = run_group(S, slot, group, &st);
+            if (o == OK_DONE) {
+                for (Req *x : group) finish(S, x, PB_OK);
+                std::lock_guard<std::mutex> g(S->mu);
+                S->batched_requests += (int64_t)group.size();
+            } else if (o == PREEMPTED) {
+                requeue = group;
+            } else {
+                // one by one
+                for (Req *x : group) {
+                    {
+                        std::lock_guard<std::mutex> g(S->mu);
+                        S->active[slot] = x;
+                        x->preempt = false;
+                    }
+                    pb_status sx = PB_OK;
+                    const Outcome ox = run(S, slot, x, &sx);
+                    if (ox == PREEMPTED)
+                        requeue.push_back(x);
+                    else
+                        finish(S, x, sx);
+                }
+            }
+        } else {
+            pb_status st = PB_OK;
+            const Outcome o = run(S, slot, q, &st);
+            if (o != PREEMPTED)
+                finish(S, q, st);
+            else
+                requeue.push_back(q);
+        }
         lk.lock();
         S->active[slot] = nullptr;
-        if (o == PREEMPTED) {
-            ++q->restarts;
+        for (auto it = requeue.rbegin(); it != requeue.rend(); ++it) {
+            ++(*it)->restarts;
             ++S->preempted;
-            S->queue.push_front(q);
+            S->queue.push_front(*it);
         }
         S->cv_work.notify_all();
     }
@@ -590,6 +808,22 @@ pb_status pb_serve_release(pb_server *S, uint64_t id) {
     }
     cudaSetDevice(prev);
     S->cv_work.notify_all();
+    return PB_OK;
+}
+
+pb_status pb_server_set_batching(pb_server *S, int32_t max_requests, double max_request_work) {
+    if (!S || max_requests < 1 || max_requests > 4096 || !(max_request_work >= 0)) return PB_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->batch_max = max_requests;
+    S->batch_work = max_request_work;
+    return PB_OK;
+}
+
+pb_status pb_serve_batch_stats(pb_server *S, int64_t *requests, int64_t *launches) {
+    if (!S) return PB_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(S->mu);
+    if (requests) *requests = S->batched_requests;
+    if (launches) *launches = S->batch_launches;
     return PB_OK;
 }
 

@@ -244,3 +244,42 @@ def test_results_resident_until_release(pb):
     srv.release(rid)
     assert srv.stats()["bytes_in_use"] == 0
     srv.close()
+
+
+def test_small_requests_coalesced(pb):
+    """Small requests that queue together run as batched launches (Galerkin members:
+    one launch for all A P, one for all P^T (A P)).  Each result matches the oracle
+    (Galerkin: the closed form, exactly); FP64 and FP32 requests never share a
+    launch.  With coalescing off the same requests run one by one."""
+    reqs = mixed_requests(pb, 3)
+    Abig, Bbig = synth.er(1 << 20, 8, seed=9)   # above the small-request bound: runs alone
+    big = (pb.csc_to_device(Abig), pb.csr_to_device(Bbig))
+    for batching in (True, False):
+        srv = pb.Server(8 << 30, max_slots=1)
+        if not batching:
+            srv.set_batching(1, 0.0)
+        # two long requests hold the only slot while the small ones queue up behind them
+        first = [srv.submit_product(*big), srv.submit_product(*big)]
+        ids = [submit(srv, r) for r in reqs]
+        for rid in first:
+            assert srv.wait(rid) == 0
+            srv.release(rid)
+
+        def check(j, C):
+            kind, A, B, dt, _, _ = reqs[j]
+            if kind == "galerkin":
+                N = round(A.nrows ** (1 / 3))
+                assert np.array_equal(dense(C), coarse_closed_form(N))
+            else:
+                assert_matches(C, oracle.spgemm(A, B), EPS["f32"])
+            assert_csr_valid(C, C.ncols)
+
+        drain(srv, ids, check)
+        st = srv.stats()
+        assert st["completed"] == len(reqs) + 2 and st["bytes_in_use"] == 0
+        if batching:
+            # at least the FP64 Galerkin group (two launches) and the FP32 group ran batched
+            assert st["batched_requests"] >= 4 and st["batch_launches"] >= 3, st
+        else:
+            assert st["batched_requests"] == 0 and st["batch_launches"] == 0, st
+        srv.close()
