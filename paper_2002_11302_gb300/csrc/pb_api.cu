@@ -60,7 +60,8 @@ struct pb_plan {
     int packed = 0;
     // workspace layout of the numeric phase
     size_t ws_keys = 0, ws_vals = 0, ws_cursor = 0, ws_status = 0, ws_ctrl = 0;
-    size_t ws_skeys = 0, ws_svals = 0, ws_hist = 0, ws_over_u = 0, ws_overp = 0, ws_overord = 0, ws_bytes = 0;
+    size_t ws_skeys = 0, ws_svals = 0, ws_hist = 0, ws_cinfo = 0, ws_over_u = 0, ws_overp = 0, ws_overord = 0,
+           ws_bytes = 0;
 };
 
 namespace {
@@ -489,6 +490,8 @@ pb_status pb_spgemm_symbolic(pb_handle *h, const pb_csc *A, const pb_csr *B, pb_
     w += align256(tuple_val_bytes(dtype) * OT);
     p->ws_hist = w;
     w += align256(4 * 256 * OC);
+    p->ws_cinfo = w;
+    w += align256(sizeof(OverChunk) * OC);
     p->ws_over_u = w;
     w += align256(8 * NO);
     p->ws_overp = w;
@@ -592,6 +595,7 @@ static OversizeArgs oversize_args(const pb_plan *p, void *workspace, const pb_pa
     o.skeys = reinterpret_cast<uint32_t *>(w + p->ws_skeys);
     o.svals = w + p->ws_svals;
     o.hist = reinterpret_cast<uint32_t *>(w + p->ws_hist);
+    o.cinfo = reinterpret_cast<OverChunk *>(w + p->ws_cinfo);
     o.over_u = reinterpret_cast<int64_t *>(w + p->ws_over_u);
     o.dense = p->over_dense;
     o.dense_shift = p->over_shift;

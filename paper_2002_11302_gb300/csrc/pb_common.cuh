@@ -98,6 +98,15 @@ struct SymbolicArgs {
 
 struct BatchDesc;
 
+// Where one OVER_CHUNK-tuple work item of an oversize bin reads and writes
+// (one 32-byte load instead of a chain of dependent list lookups).
+struct __align__(16) OverChunk {
+    int64_t main_base;  // the bin's first tuple in the main buffer (index into keys / vals)
+    int64_t scr_base;   // the bin's first tuple in the scratch buffer (index into skeys / svals)
+    int64_t start;      // the work item's first tuple within the bin
+    int32_t len, o;     // its tuples; its oversize bin
+};
+
 struct OversizeArgs {
     const int64_t *R;
     const int32_t *bin_row;
@@ -139,6 +148,9 @@ struct OversizeArgs {
     const int64_t *dev_count;
     const BatchDesc *desc;
     const int32_t *bin_prod;
+    // [c_hi - c_lo] the work items' places, filled by launch_oversize before the
+    // passes (null: each pass looks them up in the lists)
+    OverChunk *cinfo;
 };
 
 template <class T>

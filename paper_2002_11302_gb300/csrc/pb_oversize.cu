@@ -30,7 +30,8 @@ constexpr int ONW = OT / 32;
 constexpr int OWS = OVER_CHUNK / ONW;  // tuples per warp in a chunk
 
 struct ChunkRef {
-    int64_t o, bin, start, len;
+    int64_t o, start, len;
+    int64_t main_base, scr_base;  // the bin's first tuple in the main and scratch buffers
 };
 
 // End of the oversize bins and of their work items: the launch's values, or
@@ -42,23 +43,49 @@ __device__ inline uint32_t *over_hist(const OversizeArgs &a) {
     return a.dev_count ? a.keys + a.dev_count[2] : a.hist;
 }
 
-__device__ inline ChunkRef chunk_ref(const OversizeArgs &a, int64_t c) {
+// Work item c from the lists (four levels of dependent loads).
+__device__ inline ChunkRef chunk_lookup(const OversizeArgs &a, int64_t c) {
     ChunkRef r;
     r.o = a.over_chunk_bin[c];
-    r.bin = a.over_bin[r.o];
-    const int64_t N = a.R[a.bin_row[r.bin + 1]] - a.R[a.bin_row[r.bin]];
+    const int64_t bin = a.over_bin[r.o];
+    const int64_t N = a.R[a.bin_row[bin + 1]] - a.R[a.bin_row[bin]];
     r.start = (c - a.over_chunk_off[r.o]) * OVER_CHUNK;
     r.len = (N - r.start < OVER_CHUNK) ? N - r.start : OVER_CHUNK;
+    r.main_base = a.bin_off[bin] - a.tuple_base;
+    r.scr_base = a.over_tuple_off[r.o] - a.over_base;
     return r;
+}
+
+__device__ inline ChunkRef chunk_ref(const OversizeArgs &a, int64_t c) {
+    if (!a.cinfo) return chunk_lookup(a, c);
+    const OverChunk x = a.cinfo[c - a.c_lo];
+    return ChunkRef{x.o, x.start, x.len, x.main_base, x.scr_base};
+}
+
+__global__ void k_over_chunk_info(const OversizeArgs a) {
+    for (int64_t c = a.c_lo + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < a.c_hi;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        const ChunkRef r = chunk_lookup(a, c);
+        a.cinfo[c - a.c_lo] = OverChunk{r.main_base, r.scr_base, r.start, (int32_t)r.len, (int32_t)r.o};
+    }
+}
+
+// Bring the `len` tuples from index t of a bin's region into L2 (bulk prefetch).
+// Regions start at multiples of 4 tuples and are padded to them, so rounding
+// len up keeps to 16-byte granules inside the region.
+template <class T>
+__device__ inline void prefetch_tuples_l2(const T *base, int64_t t, int64_t len) {
+    const uint32_t bytes = (uint32_t)(((len + 3) & ~int64_t(3)) * (int64_t)sizeof(T));
+    if (bytes) asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(base + t), "r"(bytes) : "memory");
 }
 
 template <class TV>
 __device__ inline void pass_buffers(const OversizeArgs &a, int pass, const ChunkRef &r, const uint32_t *&sk,
                                     const TV *&sv, uint32_t *&dk, TV *&dv) {
-    uint32_t *mk = a.keys + (a.bin_off[r.bin] - a.tuple_base);
-    TV *mv = static_cast<TV *>(a.vals) + (a.bin_off[r.bin] - a.tuple_base);
-    uint32_t *xk = a.skeys + (a.over_tuple_off[r.o] - a.over_base);
-    TV *xv = static_cast<TV *>(a.svals) + (a.over_tuple_off[r.o] - a.over_base);
+    uint32_t *mk = a.keys + r.main_base;
+    TV *mv = static_cast<TV *>(a.vals) + r.main_base;
+    uint32_t *xk = a.skeys + r.scr_base;
+    TV *xv = static_cast<TV *>(a.svals) + r.scr_base;
     if ((pass & 1) == 0) {
         sk = mk; sv = mv; dk = xk; dv = xv;
     } else {
@@ -73,6 +100,9 @@ __global__ void __launch_bounds__(OT) k_over_hist(const OversizeArgs a, int pass
     uint32_t *hist = over_hist(a);
     for (int64_t c = a.c_lo + blockIdx.x; c < c_hi; c += gridDim.x) {
         const ChunkRef r = chunk_ref(a, c);
+        const bool has_next = c + gridDim.x < c_hi;
+        ChunkRef rn{};
+        if (threadIdx.x == 0 && has_next) rn = chunk_ref(a, c + gridDim.x);  // used after the count
         const uint32_t *sk;
         const TV *sv;
         uint32_t *dk;
@@ -81,6 +111,14 @@ __global__ void __launch_bounds__(OT) k_over_hist(const OversizeArgs a, int pass
         for (int i = threadIdx.x; i < 256; i += OT) h[i] = 0;
         __syncthreads();
         for (int64_t q = threadIdx.x; q < r.len; q += OT) atomicAdd(&h[(sk[r.start + q] >> shift) & 255u], 1u);
+        if (threadIdx.x == 0 && has_next) {  // the CTA's next work item into L2
+            const uint32_t *nk;
+            const TV *nv;
+            uint32_t *dk2;
+            TV *dv2;
+            pass_buffers<TV>(a, pass, rn, nk, nv, dk2, dv2);
+            prefetch_tuples_l2(nk, rn.start, rn.len);
+        }
         __syncthreads();
         for (int i = threadIdx.x; i < 256; i += OT) hist[(c - a.c_lo) * 256 + i] = h[i];
         __syncthreads();
@@ -114,6 +152,7 @@ struct ScatterSmem {
     uint32_t wc[256 * ONW];   // per (digit, warp) counts, then offsets inside the digit's run
     uint32_t cbase[256];      // first position of each digit in the chunk's staged order
     int64_t gbase[256];       // destination of a staged position i with digit d: gbase[d] + i
+    uint32_t hrow[256];       // the work item's digit offsets (loaded before the ranking)
     uint32_t sk[OVER_CHUNK];  // the chunk, staged in digit order
     TV sv[OVER_CHUNK];
 };
@@ -135,6 +174,13 @@ __global__ void __launch_bounds__(OT, 2) k_over_scatter(const OversizeArgs a, in
         uint32_t *dk;
         TV *dv;
         pass_buffers<TV>(a, pass, r, sk, sv, dk, dv);
+        // loaded now, used after the ranking: this work item's digit offsets and
+        // where the CTA's next work item lies (its tuples are then brought into L2)
+        uint32_t hv = 0;
+        if (threadIdx.x < 256) hv = hist[(c - a.c_lo) * 256 + threadIdx.x];
+        const bool has_next = c + gridDim.x < c_hi;
+        ChunkRef rn{};
+        if (threadIdx.x == 0 && has_next) rn = chunk_ref(a, c + gridDim.x);
         for (int i = threadIdx.x; i < 256 * ONW; i += OT) m.wc[i] = 0;
         __syncthreads();
         uint32_t kk[OE], lr[OE];
@@ -164,6 +210,16 @@ __global__ void __launch_bounds__(OT, 2) k_over_scatter(const OversizeArgs a, in
             lr[j] = old + __popc(peers & lanemask_lt());
             kk[j] = key;
         }
+        if (threadIdx.x < 256) m.hrow[threadIdx.x] = hv;
+        if (threadIdx.x == 0 && has_next) {
+            const uint32_t *nk;
+            const TV *nv;
+            uint32_t *dk2;
+            TV *dv2;
+            pass_buffers<TV>(a, pass, rn, nk, nv, dk2, dv2);
+            prefetch_tuples_l2(nk, rn.start, rn.len);
+            prefetch_tuples_l2(nv, rn.start, rn.len);
+        }
         __syncthreads();
         // per digit: exclusive prefix over warps (stable order inside the chunk), digit total
         if (threadIdx.x < 256) {
@@ -188,7 +244,7 @@ __global__ void __launch_bounds__(OT, 2) k_over_scatter(const OversizeArgs a, in
             for (int j = 0; j < 8; ++j) {
                 const int d = lane * 8 + j;
                 m.cbase[d] = pre;
-                m.gbase[d] = (int64_t)hist[(c - a.c_lo) * 256 + d] - pre;
+                m.gbase[d] = (int64_t)m.hrow[d] - pre;
                 pre += t[j];
             }
         }
@@ -220,8 +276,7 @@ __global__ void __launch_bounds__(OT) k_over_heads(const OversizeArgs a, int pas
     const int64_t c_hi = over_c_hi(a);
     for (int64_t c = a.c_lo + blockIdx.x; c < c_hi; c += gridDim.x) {
         const ChunkRef r = chunk_ref(a, c);
-        const uint32_t *k = (passes & 1) ? a.skeys + (a.over_tuple_off[r.o] - a.over_base)
-                                         : a.keys + (a.bin_off[r.bin] - a.tuple_base);
+        const uint32_t *k = (passes & 1) ? a.skeys + r.scr_base : a.keys + r.main_base;
         int64_t heads = 0;
         for (int64_t q = threadIdx.x; q < r.len; q += OT) {
             const int64_t p = r.start + q;
@@ -626,6 +681,10 @@ cudaError_t run_oversize(const OversizeArgs &a, int passes, int num_sms, cudaStr
     const unsigned ogrid = (unsigned)(no < g8 ? no : g8);
     cudaError_t e = cudaMemsetAsync(a.over_u + a.o_lo, 0, 8 * (size_t)no, s);
     if (e != cudaSuccess) return e;
+    if (a.cinfo) {
+        k_over_chunk_info<<<(unsigned)((nc + 255) / 256), 256, 0, s>>>(a);
+        count_launches(1);
+    }
     e = cudaFuncSetAttribute(k_over_scatter<TV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)sizeof(ScatterSmem<TV>));
     if (e != cudaSuccess) return e;
