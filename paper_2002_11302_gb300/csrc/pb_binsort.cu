@@ -451,6 +451,25 @@ __device__ inline uint4 bucket_words(uint4 c, uint32_t s) {
     return o;
 }
 
+// Bring bin nb's tuples into L2 (bulk prefetch; one thread).  A CTA calls this
+// for the bin one grid ahead of the one it takes, about the bin it takes next,
+// without taking its ticket (the look-back chain is not lengthened).  Bin
+// regions start at multiples of 4 tuples and are padded to them (16-byte
+// granules); bins above the capacity are left alone.
+template <class TV, bool PACK>
+__device__ inline void prefetch_bin_l2(const NumericArgs &p, int64_t nb, int cap) {
+    const int64_t o0 = p.bin_off[nb] - p.tuple_base, n = p.bin_off[nb + 1] - p.bin_off[nb];
+    if (n <= 0 || n > cap) return;
+    if constexpr (PACK) {
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(reinterpret_cast<const uint2 *>(p.keys) + o0),
+                     "r"((uint32_t)(n * 8)) : "memory");
+    } else {
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p.keys + o0), "r"((uint32_t)(n * 4)) : "memory");
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(static_cast<const TV *>(p.vals) + o0),
+                     "r"((uint32_t)(n * sizeof(TV))) : "memory");
+    }
+}
+
 // Value of the bin's tuple at position i (shared memory).
 template <class TV, class S>
 __device__ inline TV bin_value(const S &sm, int i) {
@@ -509,6 +528,7 @@ __global__ void __launch_bounds__(THREADS, (THREADS <= 256 ? 4 : (THREADS <= 512
         }
         int N = (int)Nfull;
         const int rows_b = row1 - row0;
+        if (tid == 32 && b + gridDim.x < p.bin_hi) prefetch_bin_l2<TV, PACK>(p, b + gridDim.x, CAP);
         // ---- load the bin (bulk copies, 16-byte granules) ---------------------------
         bool loaded = true;
         if (N > 0) {
@@ -892,6 +912,7 @@ __global__ void __launch_bounds__(THREADS, (THREADS <= 256 ? 4 : (THREADS <= 512
         }
         int N = (int)Nfull;
         const int rows_b = row1 - row0;
+        if (tid == 32 && b + gridDim.x < bin_hi) prefetch_bin_l2<TV, false>(p, b + gridDim.x, CAP);
         // ---- load the bin (bulk copies, 16-byte granules) -----------------------
         bool loaded = true;
         if (N > 0 && tid == 0) {

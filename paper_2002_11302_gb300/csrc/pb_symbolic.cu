@@ -19,30 +19,60 @@ namespace pb {
 
 namespace {
 
-// One thread per column k: f_k = nnz(A(:,k)) * nnz(B(k,:)) (Alg. 3), the
-// column index of each of its A entries, and the per-row flop (Sec. III-B):
+// Tiles of FT columns, one column per thread: f_k = nnz(A(:,k)) * nnz(B(k,:))
+// (Alg. 3).  Then the tile's A entries, which are contiguous in CSC, one per
+// thread (coalesced): the column of each entry (binary search over the
+// tile's column pointers in shared memory) and the per-row flop (Sec. III-B):
 // every A(i,k) adds nnz(B(k,:)) to row i.  Columns with more than LONG_COL
-// entries are listed for a warp-wide pass instead.
-constexpr int LONG_COL = 32;
+// entries are listed for a warp-per-column pass instead.
+constexpr int FT = 256;
+constexpr int LONG_COL = 8192;
 
 __device__ inline void add_row_flop(int64_t *R, int32_t row, int64_t lb) {
     atomicAdd(reinterpret_cast<unsigned long long *>(&R[row]), (unsigned long long)lb);
 }
 
-__global__ void k_flop_per_k(int32_t k, const int32_t *colptrA, const int32_t *rowidxA, const int32_t *rowptrB,
-                             int64_t *F, int64_t *R, int32_t *acol, int32_t *long_cols, uint32_t *n_long) {
-    for (int64_t col = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; col < k; col += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t a0 = colptrA[col], a1 = colptrA[col + 1];
-        const int64_t lb = (int64_t)rowptrB[col + 1] - rowptrB[col];
-        F[col] = (int64_t)(a1 - a0) * lb;
-        if (a1 - a0 > LONG_COL) {
-            long_cols[atomicAdd(n_long, 1u)] = (int32_t)col;
-        } else {
-            for (int32_t e = a0; e < a1; ++e) {
-                acol[e] = (int32_t)col;
-                if (lb) add_row_flop(R, rowidxA[e], lb);
+__global__ void __launch_bounds__(FT) k_flop_per_k(int32_t k, const int32_t *colptrA, const int32_t *rowidxA,
+                                                   const int32_t *rowptrB, int64_t *F, int64_t *R, int32_t *acol,
+                                                   int32_t *long_cols, uint32_t *n_long) {
+    __shared__ int32_t cp[FT + 1];
+    __shared__ int32_t lbs[FT];  // nnz(B(k,:)) of the tile's columns; -1 for a listed long column
+    const int tid = threadIdx.x;
+    const int64_t ntiles = ceil_div<int64_t>(k, FT);
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int64_t k0 = t * FT;
+        const int n = (int)(k - k0 < FT ? k - k0 : FT);
+        if (tid <= n) cp[tid] = colptrA[k0 + tid];
+        if (tid < n) {
+            const int64_t col = k0 + tid;
+            const int32_t na = colptrA[col + 1] - colptrA[col];
+            const int32_t lb = rowptrB[col + 1] - rowptrB[col];
+            F[col] = (int64_t)na * lb;
+            if (na > LONG_COL) {
+                long_cols[atomicAdd(n_long, 1u)] = (int32_t)col;
+                lbs[tid] = -1;
+            } else {
+                lbs[tid] = lb;
             }
         }
+        if (tid == 0 && n == FT) cp[FT] = colptrA[k0 + FT];
+        __syncthreads();
+        const int32_t e1 = cp[n];
+        for (int32_t e = cp[0] + tid; e < e1; e += FT) {
+            int lo = 0, hi = n;  // cp[lo] <= e < cp[hi]
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (cp[mid] <= e)
+                    lo = mid;
+                else
+                    hi = mid;
+            }
+            const int32_t lb = lbs[lo];
+            if (lb < 0) continue;  // a long column: its warp does it
+            acol[e] = (int32_t)(k0 + lo);
+            if (lb) add_row_flop(R, rowidxA[e], lb);
+        }
+        __syncthreads();
     }
 }
 
@@ -200,36 +230,16 @@ __device__ inline void entry_info(int64_t e, int64_t s, int32_t b0, int64_t lb, 
         chunk_e[c] = (c * chunk == s) ? (int32_t)e : (int32_t)(e + 1);
 }
 
-// One thread per short column (the columns of the flop pass): its entries'
-// runs start at F[k], F[k] + lb, ...
-__global__ void k_entry_pass(int32_t k, const int32_t *colptrA, const int32_t *rowidxA, const int32_t *rowptrB,
-                             const uint64_t *rowinfo, const int64_t *F, int64_t chunk, uint64_t *ainfo, int2 *aspan,
-                             int32_t *chunk_e) {
-    for (int64_t col = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; col < k; col += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t a0 = colptrA[col], a1 = colptrA[col + 1];
-        if (a1 - a0 > LONG_COL) continue;
-        const int64_t lb = (int64_t)rowptrB[col + 1] - rowptrB[col];
-        const int64_t s0 = F[col];
-        for (int32_t e = a0; e < a1; ++e)
-            entry_info(e, s0 + (e - a0) * lb, rowptrB[col], lb, chunk, rowidxA, rowinfo, ainfo, aspan, chunk_e);
-    }
-}
-
-// One warp per listed long column.
-__global__ void k_entry_long(const int32_t *colptrA, const int32_t *rowidxA, const int32_t *rowptrB,
-                             const uint64_t *rowinfo, const int64_t *F, const int32_t *long_cols,
-                             const uint32_t *n_long, int64_t chunk, uint64_t *ainfo, int2 *aspan, int32_t *chunk_e) {
-    const int lane = threadIdx.x & 31;
-    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const int64_t n = *n_long;
-    for (int64_t i = warp; i < n; i += nwarps) {
-        const int32_t col = long_cols[i];
-        const int32_t a0 = colptrA[col], a1 = colptrA[col + 1];
-        const int64_t lb = (int64_t)rowptrB[col + 1] - rowptrB[col];
-        const int64_t s0 = F[col];
-        for (int32_t e = a0 + lane; e < a1; e += 32)
-            entry_info(e, s0 + (e - a0) * lb, rowptrB[col], lb, chunk, rowidxA, rowinfo, ainfo, aspan, chunk_e);
+// One thread per A entry (coalesced), its column from the flop pass: the
+// entry's run starts at F[k] + (its position in the column) * lb.
+__global__ void k_entry_pass(int64_t nnzA, const int32_t *acol, const int32_t *colptrA, const int32_t *rowidxA,
+                             const int32_t *rowptrB, const uint64_t *rowinfo, const int64_t *F, int64_t chunk,
+                             uint64_t *ainfo, int2 *aspan, int32_t *chunk_e) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nnzA; e += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t col = acol[e];
+        const int32_t b0 = rowptrB[col];
+        const int64_t lb = (int64_t)rowptrB[col + 1] - b0;
+        entry_info(e, F[col] + (e - colptrA[col]) * lb, b0, lb, chunk, rowidxA, rowinfo, ainfo, aspan, chunk_e);
     }
 }
 
@@ -251,8 +261,8 @@ cudaError_t launch_symbolic(const SymbolicArgs &a, int64_t *scan_tmp, cudaStream
     // 1-2. per-k flop (Alg. 3), column of every A entry, per-row flop (Sec. III-B); prefixes
     if ((e = cudaMemsetAsync(a.n_long, 0, sizeof(uint32_t), s)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(a.R, 0, sizeof(int64_t) * ((size_t)a.m + 1), s)) != cudaSuccess) return e;
-    k_flop_per_k<<<grid_for(a.k, T), T, 0, s>>>(a.k, a.colptrA, a.rowidxA, a.rowptrB, a.F, a.R, a.acol, a.long_cols,
-                                               a.n_long);
+    k_flop_per_k<<<grid_for(a.k, FT), FT, 0, s>>>(a.k, a.colptrA, a.rowidxA, a.rowptrB, a.F, a.R, a.acol,
+                                                 a.long_cols, a.n_long);
     k_acol_long<<<grid_for((int64_t)a.k * 32, T), T, 0, s>>>(a.colptrA, a.rowidxA, a.rowptrB, a.long_cols, a.n_long,
                                                             a.R, a.acol);
     if ((e = scan_i64(a.F, a.k, scan_tmp, s)) != cudaSuccess) return e;
@@ -310,12 +320,9 @@ cudaError_t launch_chunk_table(const SymbolicArgs &a, int64_t nchunks, int64_t c
     k_set_i32<<<1, 1, 0, s>>>(chunk_e + nchunks, (int32_t)a.nnzA);
     count_launches(1);
     if (a.nnzA > 0) {
-        k_entry_pass<<<grid_for(a.k, 256), 256, 0, s>>>(a.k, a.colptrA, a.rowidxA, a.rowptrB, a.rowinfo, a.F, chunk,
-                                                        a.ainfo, a.aspan, chunk_e);
-        k_entry_long<<<grid_for((int64_t)a.k * 32, 256), 256, 0, s>>>(a.colptrA, a.rowidxA, a.rowptrB, a.rowinfo, a.F,
-                                                                      a.long_cols, a.n_long, chunk, a.ainfo, a.aspan,
-                                                                      chunk_e);
-        count_launches(2);
+        k_entry_pass<<<grid_for(a.nnzA, 256), 256, 0, s>>>(a.nnzA, a.acol, a.colptrA, a.rowidxA, a.rowptrB,
+                                                           a.rowinfo, a.F, chunk, a.ainfo, a.aspan, chunk_e);
+        count_launches(1);
     }
     return cudaGetLastError();
 }
