@@ -399,18 +399,18 @@ __device__ void stream_oversize_bin(const NumericArgs &p, int64_t b, int32_t row
 //      where the row changes.
 // ---------------------------------------------------------------------------
 // PACK: the bin arrives as packed {key, value bits} pairs (4-byte values) in
-// vin.  Phase A takes each pair into registers and phases C/D write the value
-// at the tuple's sorted position over the start of vin (as floats), so phase F
-// reads values in sorted order.  The radix path reads the pairs in place.
+// pin; phase A keeps each key in a register and stores the value into vin at
+// the tuple's position, so everything after phase A is as for separate arrays
+// (the radix path's first pass reads the keys from pin).
 template <int CAP, int THREADS, class TV, bool PACK = false>
 struct BinSmem {
     static constexpr int NW = THREADS / 32;
     uint32_t kin[CAP];     // the bin's keys (bulk copy), then its sorted keys
-    typename std::conditional<PACK, uint2, TV>::type vin[CAP];  // the bin's values or pairs (bulk copy)
+    TV vin[CAP];           // the bin's values (bulk copy; PACK: written by phase A)
     uint32_t pk[CAP];      // multi-tuple buckets: low key bits << log2(CAP) | position; radix: keys
     uint16_t fidx[CAP];    // position in the bin of each sorted tuple
     uint16_t sidx2[CAP];   // radix: positions
-    uint32_t cnt[CAP];     // bucket counters, then start | size << 16; radix digit counters
+    alignas(16) uint32_t cnt[CAP];  // bucket counters, then start | size << 16; radix digit counters (uint4 access)
     int64_t scratch[40];
     uint32_t wtot[NW];     // per warp: bucket-count sums (B), merged entries (E)
     uint64_t bar;
@@ -418,6 +418,7 @@ struct BinSmem {
     int64_t prefix;
     uint32_t big;
     int32_t ok;
+    alignas(16) uint2 pin[PACK ? CAP : 1];  // PACK: the bin's {key, value bits} pairs (bulk copy)
 };
 
 __device__ inline uint32_t lanemask_le() {
@@ -470,19 +471,13 @@ __device__ inline void prefetch_bin_l2(const NumericArgs &p, int64_t nb, int cap
     }
 }
 
-// Value of the bin's tuple at position i (shared memory).
-template <class TV, class S>
-__device__ inline TV bin_value(const S &sm, int i) {
-    if constexpr (sizeof(sm.vin[0]) == 8 && sizeof(TV) == 4)
-        return __uint_as_float(sm.vin[i].y);  // packed pair
-    else
-        return sm.vin[i];
-}
 
 template <int CAP, int THREADS, class TV, class OV, bool PACK>
 __global__ void __launch_bounds__(THREADS, (THREADS <= 256 ? 4 : (THREADS <= 512 ? 2 : 1))) k_binsort(const NumericArgs p) {
     using S = BinSmem<CAP, THREADS, TV, PACK>;
     static_assert(!PACK || sizeof(TV) == 4, "packed tuples hold 4-byte values");
+    static_assert(offsetof(S, cnt) % 16 == 0 && offsetof(S, vin) % 16 == 0 && offsetof(S, pin) % 16 == 0,
+                  "16-byte accesses and bulk-copy destinations");
     constexpr int NW = THREADS / 32;
     constexpr int E = CAP / THREADS;  // tuples per thread in A-D
     constexpr int WS = CAP / NW;      // sorted positions per warp in E-F
@@ -536,7 +531,7 @@ __global__ void __launch_bounds__(THREADS, (THREADS <= 256 ? 4 : (THREADS <= 512
                 const uint32_t n4 = (uint32_t)((N + 3) & ~3);
                 if constexpr (PACK) {
                     mbar_arrive_expect_tx(&sm.bar, n4 * 8u);
-                    bulk_g2s(sm.vin, reinterpret_cast<const uint2 *>(p.keys) + off, n4 * 8u, &sm.bar);
+                    bulk_g2s(sm.pin, reinterpret_cast<const uint2 *>(p.keys) + off, n4 * 8u, &sm.bar);
                 } else {
                     mbar_arrive_expect_tx(&sm.bar, n4 * 4u + n4 * (uint32_t)sizeof(TV));
                     bulk_g2s(sm.kin, p.keys + off, n4 * 4u, &sm.bar);
@@ -554,27 +549,24 @@ __global__ void __launch_bounds__(THREADS, (THREADS <= 256 ? 4 : (THREADS <= 512
         }
         const uint32_t *sk = sm.kin;   // sorted keys
         const uint16_t *si = sm.fidx;  // their positions in the bin
-        float *sval = reinterpret_cast<float *>(sm.vin);  // PACK: values in sorted order (not radix)
-        bool radix = false;
         if (N > 0) {
             const uint32_t kmax = (uint32_t)((((uint64_t)rows_b) << colbits) - 1u);
             const int rbits = kmax ? 32 - __clz(kmax) : 0;
             const int shift = rbits > LOG_CAP ? rbits - LOG_CAP : 0;  // <= 32 - LOG_CAP
             const uint32_t lowmask = (1u << shift) - 1u;
             // ---- A: bucket counts and arrival ranks ------------------------------------
-            uint32_t kr[E], rk[E], vr[E];
+            uint32_t kr[E], rk[E];
             bool mine_big = false;
 #pragma unroll
             for (int j = 0; j < E; ++j) {
                 const int q = tid + j * THREADS;
                 kr[j] = 0;
                 rk[j] = 0;
-                vr[j] = 0;
                 if (q < N) {
                     if constexpr (PACK) {
-                        const uint2 t = sm.vin[q];
+                        const uint2 t = sm.pin[q];
                         kr[j] = t.x;
-                        vr[j] = t.y;
+                        sm.vin[q] = __uint_as_float(t.y);
                     } else {
                         kr[j] = sm.kin[q];
                     }
@@ -584,8 +576,7 @@ __global__ void __launch_bounds__(THREADS, (THREADS <= 256 ? 4 : (THREADS <= 512
             }
             if (mine_big) sm.big = 1;
             __syncthreads();
-            radix = sm.big != 0;
-            if (!radix) {
+            if (sm.big == 0) {
                 // ---- B: bucket starts ---------------------------------------------------
                 {
                     uint4 *c0 = reinterpret_cast<uint4 *>(sm.cnt + 4 * tid);
@@ -617,10 +608,7 @@ __global__ void __launch_bounds__(THREADS, (THREADS <= 256 ? 4 : (THREADS <= 512
                         const uint32_t start = w & 0xffffu;
                         if ((w >> 16) == 1u) {
                             sm.kin[start] = kr[j];
-                            if constexpr (PACK)
-                                sval[start] = __uint_as_float(vr[j]);
-                            else
-                                sm.fidx[start] = (uint16_t)q;
+                            sm.fidx[start] = (uint16_t)q;
                         } else {
                             sm.pk[start + rk[j]] = ((kr[j] & lowmask) << LOG_CAP) | (uint32_t)q;
                             multi |= 1u << j;
@@ -639,10 +627,7 @@ __global__ void __launch_bounds__(THREADS, (THREADS <= 256 ? 4 : (THREADS <= 512
                         int rank = start;
                         for (int r = start; r < end; ++r) rank += sm.pk[r] < mine;
                         sm.kin[rank] = kr[j];
-                        if constexpr (PACK)
-                            sval[rank] = __uint_as_float(vr[j]);
-                        else
-                            sm.fidx[rank] = (uint16_t)q;
+                        sm.fidx[rank] = (uint16_t)q;
                     }
                 }
                 __syncthreads();
@@ -665,7 +650,7 @@ __global__ void __launch_bounds__(THREADS, (THREADS <= 256 ? 4 : (THREADS <= 512
                         const bool valid = q < N;
                         uint32_t key = 0u;
                         if constexpr (PACK) {  // the first pass reads the packed input
-                            if (valid) key = srci ? srck[q] : sm.vin[q].x;
+                            if (valid) key = srci ? srck[q] : sm.pin[q].x;
                         } else {
                             if (valid) key = srck[q];
                         }
@@ -748,12 +733,7 @@ __global__ void __launch_bounds__(THREADS, (THREADS <= 256 ? 4 : (THREADS <= 512
         if (!sm.ok) continue;
         // ---- F: merged entries and row pointers ---------------------------------------
         // value of the tuple at sorted position i
-        auto value_at = [&](int i) -> double {
-            if constexpr (PACK)
-                return (double)(radix ? bin_value<TV>(sm, si[i]) : sval[i]);
-            else
-                return (double)bin_value<TV>(sm, si[i]);
-        };
+        auto value_at = [&](int i) -> double { return (double)sm.vin[si[i]]; };
         const int64_t P = sm.prefix;
         int64_t running = P + wbase;  // C position of the segment's first head
         uint32_t last = before;
