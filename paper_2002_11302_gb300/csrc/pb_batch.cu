@@ -171,12 +171,13 @@ void carve_tail(BatchWs &w, char *base, size_t fixed, size_t ws_bytes, int32_t c
     w.tuple_cap = 0;
     if (ws_bytes <= fixed + kSlack + 8 * ((size_t)count + 4)) return;
     const size_t rem = ws_bytes - fixed - kSlack - 8 * ((size_t)count + 4);
-    // per tuple slot: 4 key bytes, tb value bytes, 8/MIN_CHUNK bytes of work-item
+    // Per tuple slot: 4 key bytes, tb value bytes, 8/MIN_CHUNK bytes of work-item
     // table and the oversize-row arrays (44 bytes per BATCH_MIN_CAPACITY slots,
-    // 4 per OVER_CHUNK / 2); each array rounds up to 256 bytes
+    // 4 per OVER_CHUNK / 2).  Leaving out the arrays' rounding to 256 bytes makes
+    // this an upper bound, so stepping down finds the largest count that fits,
+    // which is at least the count pb_spgemm_batch_query sized the workspace for.
     const double per = 4.0 + (double)tb + 8.0 / MIN_CHUNK + 44.0 / BATCH_MIN_CAPACITY + 8.0 / OVER_CHUNK;
-    const double usable = (double)rem - 16.0 * 256.0 - 3000.0;
-    int64_t tuples = usable > 0 ? (int64_t)(usable / per) : 0;
+    int64_t tuples = (int64_t)((double)rem / per);
     tuples &= ~int64_t(3);
     while (tuples > 0 && fixed + tail_bytes(tuples, count, tb) > ws_bytes) tuples -= 4;
     if (tuples <= 0) return;

@@ -308,6 +308,29 @@ def test_batch_hub_row_in_too_wide_product_rejected(pb):
     assert_matches(C, oracle.spgemm(A, B), EPS["f64"])
 
 
+def test_batch_exact_queried_workspace_every_row_its_own_bin(pb):
+    """A workspace of exactly the queried size suffices when every row is a bin of
+    its own.  At capacity 2048, rows of 1250..1800 tuples (above half the capacity)
+    each make a bin and leave the query 8 tuples of slack; one product's rows of
+    3000 tuples are hub rows."""
+    rng = np.random.default_rng(7)
+    probs = []
+    for rows, k, n in ((4, 100, 15), (3, 60, 30), (6, 50, 25), (2, 100, 30)):   # row flop 1500, 1800, 1250, 3000
+        A = synth.coo_to_csc(rows, k, np.repeat(np.arange(rows), k), np.tile(np.arange(k), rows),
+                             rng.uniform(-1, 1, rows * k))
+        Bd = rng.uniform(-1, 1, (k, n))
+        r, c = np.nonzero(Bd)
+        probs.append((A, synth.coo_to_csr(k, n, r, c, Bd[r, c])))
+    handle = pb.Handle()
+    pb.set_tuning(all_classes(probs, 2048), handle)
+    As = [pb.csc_to_device(A) for A, _ in probs]
+    Bs = [pb.csr_to_device(B) for _, B in probs]
+    bt = pb.Batch(As, Bs, handle=handle)
+    bt.workspace_bytes -= 256   # the binding's margin off: exactly what the query reported
+    bt.run()
+    check_all(bt, probs, EPS["f64"])
+
+
 def test_batch_workspace_too_small(pb):
     probs = [synth.er(3000, 8, seed=12), synth.er(2000, 5, seed=13)]
     handle = pb.Handle()
